@@ -1,0 +1,173 @@
+/*
+ * rve.h -- C ABI of the GB300 ringing-free FFT homogenisation solver.
+ *
+ * The library solves the small-strain periodic cell (RVE) problem of
+ * "Non-convex, ringing-free, FFT-accelerated solver using an incremental
+ * approximate energy functional" (arXiv 2207.10657):
+ *
+ *   find the strain field eps = E + eps~ (Sec. 2, Eq. (1)) such that
+ *   G : sigma(eps) = 0 (Eq. (6)), with G the compatibility projection built
+ *   from the linear finite-element (ringing-free) gradient (Sec. 2.1,
+ *   Eq. (9)), sigma the isotropic damage law of Appendix A, solved by the
+ *   trust-region Newton-CG method of Algorithm 2 whose ratio test uses the
+ *   first-order incremental energy (Sec. 2.2.1, Eqs. (18)-(19)) and whose
+ *   sub-problem is Steihaug CG (Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grid: dims[0] = Nx, dims[1] = Ny, dims[2] = Nz (ignored for ndim = 2),
+ *    unit voxels, periodic.  Nvox = Nx*Ny(*Nz).  Every dim must be even,
+ *    >= 2, <= 1024 and have no prime factor other than 2, 3 and 5.
+ *  - Fields are structure-of-arrays, component-major: element (c, z, y, x)
+ *    at offset ((c*Nz + z)*Ny + y)*Nx + x, x fastest.  Components are
+ *    Mandel-orthonormal: 3D (11, 22, 33, sqrt2*23, sqrt2*13, sqrt2*12),
+ *    2D plane strain (11, 22, sqrt2*12).  ncomp = 6 (3D) or 3 (2D).
+ *  - Real type: float when the context was created with precision 32,
+ *    double with precision 64.  Pointers named *_dev are DEVICE pointers,
+ *    owned by the caller, 16-byte aligned, read/written on the context's
+ *    stream; the call returns before the device work completes unless it
+ *    returns scalars to the host (those calls synchronise the stream).
+ *  - Pointers named *_host are host pointers (pinned or pageable).
+ *  - Errors: every call returns an rve_status; nothing aborts, traps or
+ *    throws.  rve_last_error() gives a message for the last failure.
+ *  - Reductions (energies, CG scalars, the trust-region ratio) are FP64 on
+ *    the device whatever the field precision.
+ */
+#ifndef RVE_H
+#define RVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rve_ctx* rve_t; /* opaque; owned by the library */
+
+typedef enum {
+  RVE_OK = 0,
+  RVE_ERR_ARG = -1,           /* invalid argument (size, pointer, option) */
+  RVE_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+  RVE_ERR_OOM = -3,           /* device allocation failed */
+  RVE_ERR_NOT_CONVERGED = -4, /* iteration caps reached */
+  RVE_ERR_NONFINITE = -5,     /* NaN/Inf met in a reduction */
+  RVE_ERR_TIMEOUT = -6        /* a bounded device wait gave up */
+} rve_status;
+
+/* One material phase, indexed by the phase id stored per voxel.
+ * Isotropic elasticity (E, nu); if damaging != 0, isotropic damage
+ * E -> (1-D) E (Eq. (22)) driven by the tension strain measure
+ * kappa = |eps^(t)| (Eq. (A.1)), bilinear law (Eq. (A.3)) read as
+ * D = kappaf (kappa - kappa0) / (kappa (kappaf - kappa0)) on
+ * (kappa0, kappaf), 0 below, 1 from kappaf on. */
+typedef struct {
+  double E, nu;
+  int damaging;
+  double kappa0, kappaf;
+} rve_phase;
+
+/* Solver options (Algorithm 2 hyper-parameters; the paper gives no values). */
+typedef struct {
+  double eta_eq;      /* converged when |G:sigma| / |sigma| <= eta_eq */
+  double eta_nr;      /* ... or |d_eps| / |eps| <= eta_nr (0 disables) */
+  double eta_cg;      /* relative Steihaug-CG tolerance |r| <= eta_cg |g| */
+  double eta_up;      /* accept a trial step when rho_bar > eta_up */
+  double R0, Rmax;    /* initial / maximum trust radius (unnormalised norm) */
+  int max_nr, max_cg; /* Newton and CG iteration caps */
+  double restart_thr; /* Powell restart threshold, Eq. (20): 0.2 */
+  int precision;      /* 32 (FP32 fields) or 64 (FP64 fields) */
+} rve_solver_opts;
+
+/* Per-load-step statistics. */
+typedef struct {
+  int nr_iters, cg_iters, hv_products, restarts, rejected, boundary_hits;
+  int converged;
+  double rel_residual; /* |G:sigma| / |sigma| at exit */
+  double R;            /* trust radius at exit */
+  double mean_stress[6], mean_strain[6];
+} rve_step_report;
+
+/* Fill opts with defaults: eta_eq 1e-6, eta_nr 0, eta_cg 1e-2, eta_up 0.1,
+ * R0 = Rmax = 0 (meaning "10 sqrt(Nvox) |dE|" at the first load step),
+ * max_nr 50, max_cg 1000, restart_thr 0.2, precision 32. */
+void rve_default_opts(rve_solver_opts* opts);
+
+/* Create a context.  Sec. 2 (cell, strain split), Appendix A (phases).
+ *  dims, ndim     grid (see conventions); ndim 2 = plane strain.
+ *  phase_ids_dev  Nvox uint8 phase ids (device); copied, may be freed after.
+ *  phases_host    nphase entries (1..255), copied.
+ *  opts_host      may be NULL for defaults; copied.
+ *  stream         cudaStream_t (as void*) all work is issued on; NULL =
+ *                 the legacy default stream.
+ *  out            receives the handle.
+ * Allocates every workspace (spectra, CG vectors, FP64 scalars) up front;
+ * fails with RVE_ERR_OOM if the device cannot hold them.  The state starts
+ * at eps = 0, kappa_n = 0, all components strain-controlled. */
+rve_status rve_create(const int dims[3], int ndim, const uint8_t* phase_ids_dev,
+                      const rve_phase* phases_host, int nphase,
+                      const rve_solver_opts* opts_host, void* stream, rve_t* out);
+
+/* Set the state: total strain (ncomp x Nvox, real type of the context) and
+ * committed history kappa_n (Nvox floats, NULL = 0).  Recomputes sigma and
+ * D at the state (Appendix A, with kappa = max(kappa_n, kappa(eps))). */
+rve_status rve_set_state(rve_t, const void* strain_dev, const float* kappa_hist_dev);
+
+/* Copy out the state; any pointer may be NULL.  stress_dev receives sigma
+ * at the state, damage_dev the damage D (Nvox floats). */
+rve_status rve_get_state(rve_t, void* strain_dev, float* kappa_dev, void* stress_dev,
+                         float* damage_dev);
+
+/* Replace the frozen damage field used by rve_hessp (Nvox floats in [0,1]).
+ * For benchmarking the Hessian-vector product on a damage snapshot. */
+rve_status rve_set_damage(rve_t, const float* damage_dev);
+
+/* Stress-controlled mean components (zero mean stress): free_mask[c] != 0
+ * for Mandel component c.  Sets Ghat(0) = P_free (mixed control, Sec. 3.3). */
+rve_status rve_set_free_mask(rve_t, const uint8_t free_mask_host[6]);
+
+/* Hessian-vector product of Eq. (8) with the secant tangent frozen at the
+ * state: out = G : ((1 - D) C : v).  v_dev, out_dev: ncomp x Nvox real; they
+ * may alias.  The product is: tangent (Eq. (13)), forward real FFT,
+ * per-frequency projection Ghat(k) from the FE gradient (Eqs. (5), (9)),
+ * inverse FFT. */
+rve_status rve_hessp(rve_t, const void* v_dev, void* out_dev);
+
+/* Projection alone, out = G : v (Eqs. (4)-(5)).  May alias. */
+rve_status rve_project(rve_t, const void* v_dev, void* out_dev);
+
+/* Energy quantities of a trial increment p (ncomp x Nvox, NULL = 0) from
+ * the state eps (Sec. 2.2.1, Algorithm 2):
+ *   dW_bar = 1/2 (sigma(eps) + sigma(eps + p)) : p        (Eq. (18))
+ *   dm     = sigma(eps) : p + 1/2 p : (1-D) C : p           (Delta m)
+ *   grad_dev (may be NULL) = G : sigma(eps + p)             (Eq. (12))
+ * dW_bar_host / dm_host may be NULL.  Synchronises the stream. */
+rve_status rve_energy_grad(rve_t, const void* p_dev, double* dW_bar_host, double* dm_host,
+                           void* grad_dev);
+
+/* One load step of Algorithm 2: eps += dE (uniform, strain-controlled
+ * components), optionally eps += init_incr (a compatible warm-start
+ * fluctuation increment, ncomp x Nvox, NULL = none), then trust-region
+ * Newton iterations with Steihaug CG until converged; on convergence
+ * kappa_n <- max(kappa_n, kappa(eps)).  free_mask_host may be NULL (keep the
+ * current mask).  rep_host may be NULL.  Returns RVE_ERR_NOT_CONVERGED
+ * (state kept, history not committed) when max_nr is exhausted. */
+rve_status rve_solve_step(rve_t, const double dE_host[6], const uint8_t free_mask_host[6],
+                          const void* init_incr_dev, rve_step_report* rep_host);
+
+/* Message of the last error on this context (static storage; never NULL). */
+const char* rve_last_error(rve_t);
+
+/* Number of Hessian-vector products and of kernel launches issued by this
+ * context since creation (counters for benchmarks). */
+long long rve_hv_count(rve_t);
+long long rve_launch_count(rve_t);
+
+/* Free the context and its workspaces.  NULL is ignored. */
+void rve_destroy(rve_t);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RVE_H */

@@ -32,6 +32,8 @@ from .fourier import (
     ifft,
     dft_naive,
     gradient_symbol,
+    gradient_symbol_at,
+    project_one,
     project_hat,
     project,
 )
@@ -51,7 +53,7 @@ from .solver import steihaug_cg, TRParams, trust_region_step, load_path
 
 __all__ = [
     "mandel_to_tensor", "tensor_to_mandel", "ncomp_of", "normal_comps",
-    "fft", "ifft", "dft_naive", "gradient_symbol", "project_hat", "project",
+    "fft", "ifft", "dft_naive", "gradient_symbol", "gradient_symbol_at", "project_one", "project_hat", "project",
     "Phase", "lame", "PhaseParams", "elastic_stress", "principal_strains",
     "kappa_of_strain", "damage_of_kappa", "evaluate", "tangent_apply",
     "RVE", "steihaug_cg", "TRParams", "trust_region_step", "load_path",

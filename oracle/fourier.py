@@ -94,6 +94,36 @@ def gradient_symbol(shape):
     return out
 
 
+def gradient_symbol_at(k, dims):
+    """Dhat at one frequency k = (kx, ky[, kz]) of a grid dims = (Nx, Ny[, Nz])."""
+    d = len(dims)
+    out = np.ones(d, dtype=np.complex128)
+    for alpha in range(d):
+        for beta in range(d):
+            n, kb = dims[beta], int(k[beta]) % dims[beta]
+            e = np.exp(2j * np.pi * kb / n)
+            if beta == alpha:
+                fac = 0.0 if kb == 0 else e - 1.0
+            else:
+                fac = 0.0 if 2 * kb == n else (1.0 + e) / 2.0
+            out[alpha] *= fac
+    return out
+
+
+def project_one(zeta, dhat):
+    """Ghat(k) : zeta for a single frequency k != 0 (Mandel vector zeta,
+    symbol dhat); 0 where dhat = 0."""
+    t = mandel_to_tensor(np.asarray(zeta, dtype=np.complex128).reshape(-1, 1))[0]
+    nrm = np.sqrt(np.sum(np.abs(dhat) ** 2))
+    if nrm == 0.0:
+        return np.zeros(len(zeta), dtype=np.complex128)
+    n = dhat / nrm
+    v = t @ np.conj(n)
+    s = np.conj(n) @ v
+    out = np.outer(n, v) + np.outer(v, n) - s * np.outer(n, n)
+    return tensor_to_mandel(out[None])[:, 0]
+
+
 def project_hat(zeta_hat, dhat, free_mask):
     """Apply Ghat(k) at every frequency to a Mandel spectrum (ncomp, *shape).
 

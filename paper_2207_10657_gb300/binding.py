@@ -1,0 +1,173 @@
+"""ctypes binding of librve.so (include/rve.h), same names as the C ABI.
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the stream.  There is no CPU
+fallback: if the library is missing or no GPU is present the calls raise.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librve.so")
+
+RVE_OK = 0
+STATUS = {0: "RVE_OK", -1: "RVE_ERR_ARG", -2: "RVE_ERR_CUDA", -3: "RVE_ERR_OOM",
+          -4: "RVE_ERR_NOT_CONVERGED", -5: "RVE_ERR_NONFINITE", -6: "RVE_ERR_TIMEOUT"}
+
+
+class rve_phase(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("damaging", ctypes.c_int),
+                ("kappa0", ctypes.c_double), ("kappaf", ctypes.c_double)]
+
+
+class rve_solver_opts(ctypes.Structure):
+    _fields_ = [("eta_eq", ctypes.c_double), ("eta_nr", ctypes.c_double), ("eta_cg", ctypes.c_double),
+                ("eta_up", ctypes.c_double), ("R0", ctypes.c_double), ("Rmax", ctypes.c_double),
+                ("max_nr", ctypes.c_int), ("max_cg", ctypes.c_int), ("restart_thr", ctypes.c_double),
+                ("precision", ctypes.c_int)]
+
+
+class rve_step_report(ctypes.Structure):
+    _fields_ = [("nr_iters", ctypes.c_int), ("cg_iters", ctypes.c_int), ("hv_products", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("rejected", ctypes.c_int), ("boundary_hits", ctypes.c_int),
+                ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double), ("R", ctypes.c_double),
+                ("mean_stress", ctypes.c_double * 6), ("mean_strain", ctypes.c_double * 6)]
+
+
+class RveError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+# (name, restype, argtypes)
+_SIGS = [
+    ("rve_default_opts", None, [ctypes.POINTER(rve_solver_opts)]),
+    ("rve_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.POINTER(rve_phase), ctypes.c_int, ctypes.POINTER(rve_solver_opts),
+                                  ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("rve_set_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("rve_get_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p]),
+    ("rve_set_damage", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("rve_set_free_mask", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint8)]),
+    ("rve_hessp", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("rve_project", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("rve_energy_grad", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    ("rve_solve_step", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_uint8), ctypes.c_void_p,
+                                      ctypes.POINTER(rve_step_report)]),
+    ("rve_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("rve_hv_count", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("rve_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("rve_destroy", None, [ctypes.c_void_p]),
+]
+
+EXPORTED = [n for n, _, _ in _SIGS]
+
+
+def lib(path=None):
+    """Load librve.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} not found: build it with paper_2207_10657_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(p)
+    for name, res, args in _SIGS:
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = L
+    return L
+
+
+def check(status, handle=None):
+    if status != RVE_OK:
+        msg = lib().rve_last_error(handle).decode()
+        raise RveError(status, msg)
+
+
+# ----------------------------------------------------------------- wrappers
+def rve_default_opts():
+    o = rve_solver_opts()
+    lib().rve_default_opts(ctypes.byref(o))
+    return o
+
+
+def rve_create(dims, ndim, phase_ids_ptr, phases, opts=None, stream=0):
+    d = (ctypes.c_int * 3)(*(list(dims) + [1] * (3 - len(dims))))
+    arr = (rve_phase * len(phases))(*[rve_phase(*p) for p in phases])
+    h = ctypes.c_void_p()
+    st = lib().rve_create(d, ndim, ctypes.c_void_p(phase_ids_ptr), arr, len(phases),
+                          ctypes.byref(opts) if opts is not None else None,
+                          ctypes.c_void_p(stream), ctypes.byref(h))
+    check(st, None)
+    return h
+
+
+def rve_set_state(h, strain_ptr, kappa_ptr=0):
+    check(lib().rve_set_state(h, ctypes.c_void_p(strain_ptr), ctypes.c_void_p(kappa_ptr or None)), h)
+
+
+def rve_get_state(h, strain_ptr=0, kappa_ptr=0, stress_ptr=0, damage_ptr=0):
+    check(lib().rve_get_state(h, ctypes.c_void_p(strain_ptr or None), ctypes.c_void_p(kappa_ptr or None),
+                              ctypes.c_void_p(stress_ptr or None), ctypes.c_void_p(damage_ptr or None)), h)
+
+
+def rve_set_damage(h, damage_ptr):
+    check(lib().rve_set_damage(h, ctypes.c_void_p(damage_ptr)), h)
+
+
+def rve_set_free_mask(h, mask):
+    m = (ctypes.c_uint8 * 6)(*[1 if x else 0 for x in (list(mask) + [0] * (6 - len(mask)))])
+    check(lib().rve_set_free_mask(h, m), h)
+
+
+def rve_hessp(h, v_ptr, out_ptr):
+    check(lib().rve_hessp(h, ctypes.c_void_p(v_ptr), ctypes.c_void_p(out_ptr)), h)
+
+
+def rve_project(h, v_ptr, out_ptr):
+    check(lib().rve_project(h, ctypes.c_void_p(v_ptr), ctypes.c_void_p(out_ptr)), h)
+
+
+def rve_energy_grad(h, p_ptr=0, grad_ptr=0):
+    dW, dm = ctypes.c_double(), ctypes.c_double()
+    check(lib().rve_energy_grad(h, ctypes.c_void_p(p_ptr or None), ctypes.byref(dW), ctypes.byref(dm),
+                                ctypes.c_void_p(grad_ptr or None)), h)
+    return dW.value, dm.value
+
+
+def rve_solve_step(h, dE, free_mask=None, init_ptr=0, raise_on_error=True):
+    de = (ctypes.c_double * 6)(*(list(dE) + [0.0] * (6 - len(dE))))
+    fm = None
+    if free_mask is not None:
+        fm = (ctypes.c_uint8 * 6)(*[1 if x else 0 for x in (list(free_mask) + [0] * (6 - len(free_mask)))])
+    rep = rve_step_report()
+    st = lib().rve_solve_step(h, de, fm, ctypes.c_void_p(init_ptr or None), ctypes.byref(rep))
+    if raise_on_error:
+        check(st, h)
+    return st, rep
+
+
+def rve_last_error(h):
+    return lib().rve_last_error(h).decode()
+
+
+def rve_hv_count(h):
+    return lib().rve_hv_count(h)
+
+
+def rve_launch_count(h):
+    return lib().rve_launch_count(h)
+
+
+def rve_destroy(h):
+    lib().rve_destroy(h)

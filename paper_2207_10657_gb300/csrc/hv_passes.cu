@@ -1,0 +1,503 @@
+// Spectral passes of the Hessian-vector product and of the projection:
+//   x-forward (tangent fused) -> y-forward -> z-forward + projection +
+//   z-inverse -> y-inverse -> x-inverse (+ fused FP64 dot product).
+// 2D: x-forward -> y-forward + projection + y-inverse -> x-inverse.
+//
+// Sec. 2.1: G : zeta = F^-1{ Ghat(k) : F{zeta} } (Eq. (5)), Ghat from the
+// linear finite-element gradient symbol through Eq. (9); the Hessian-vector
+// product of Eq. (8) applies the tangent first, then the projection.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "hv_passes.cuh"
+
+namespace rve {
+
+constexpr int kXThreads = 256, kXEpt = 16;  // x passes
+constexpr int kYThreads = 256, kYEpt = 16;  // y columns, 2D y+projection
+constexpr int kZThreads = 512, kZEpt = 24;  // z + projection
+constexpr int kSmemCap = 100 * 1024;        // dynamic shared memory cap per block
+
+// ------------------------------------------------------------ projection
+// Ghat(k) : zeta for one frequency, Mandel components m (complex).
+// n = Dhat/|Dhat|, v = zeta n*, s = n*^T zeta n*,
+// Ghat:zeta = n (x) v + v (x) n - s n (x) n.  Ghat = 0 where Dhat = 0
+// (k != 0); Ghat(0) keeps the stress-controlled (free) components.
+template <typename R>
+__device__ __forceinline__ void project3(Cx<R> (&m)[6], Cx<R> d0, Cx<R> d1, Cx<R> d2, bool k0,
+                                         unsigned free_mask) {
+  using C = Cx<R>;
+  if (k0) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+      if (!((free_mask >> c) & 1u)) m[c] = C{0, 0};
+    return;
+  }
+  const R n2 = d0.x * d0.x + d0.y * d0.y + d1.x * d1.x + d1.y * d1.y + d2.x * d2.x + d2.y * d2.y;
+  if (n2 == (R)0) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) m[c] = C{0, 0};
+    return;
+  }
+  const R inv = (R)1 / sqrt(n2);
+  const C n[3] = {cscale(d0, inv), cscale(d1, inv), cscale(d2, inv)};
+  const R is2 = (R)0.70710678118654752440, s2 = (R)1.41421356237309504880;
+  const C t00 = m[0], t11 = m[1], t22 = m[2];
+  const C t12 = cscale(m[3], is2), t02 = cscale(m[4], is2), t01 = cscale(m[5], is2);
+  // v_i = sum_j T_ij conj(n_j)
+  const C v0 = cadd(cadd(cmulc(t00, n[0]), cmulc(t01, n[1])), cmulc(t02, n[2]));
+  const C v1 = cadd(cadd(cmulc(t01, n[0]), cmulc(t11, n[1])), cmulc(t12, n[2]));
+  const C v2 = cadd(cadd(cmulc(t02, n[0]), cmulc(t12, n[1])), cmulc(t22, n[2]));
+  // s = sum_i conj(n_i) v_i
+  const C s = cadd(cadd(cmulc(v0, n[0]), cmulc(v1, n[1])), cmulc(v2, n[2]));
+  auto o = [&](C ni, C nj, C vi, C vj) { return csub(cadd(cmul(ni, vj), cmul(vi, nj)), cmul(s, cmul(ni, nj))); };
+  m[0] = o(n[0], n[0], v0, v0);
+  m[1] = o(n[1], n[1], v1, v1);
+  m[2] = o(n[2], n[2], v2, v2);
+  m[3] = cscale(o(n[1], n[2], v1, v2), s2);
+  m[4] = cscale(o(n[0], n[2], v0, v2), s2);
+  m[5] = cscale(o(n[0], n[1], v0, v1), s2);
+}
+
+template <typename R>
+__device__ __forceinline__ void project2(Cx<R> (&m)[3], Cx<R> d0, Cx<R> d1, bool k0, unsigned free_mask) {
+  using C = Cx<R>;
+  if (k0) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (!((free_mask >> c) & 1u)) m[c] = C{0, 0};
+    return;
+  }
+  const R n2 = d0.x * d0.x + d0.y * d0.y + d1.x * d1.x + d1.y * d1.y;
+  if (n2 == (R)0) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m[c] = C{0, 0};
+    return;
+  }
+  const R inv = (R)1 / sqrt(n2);
+  const C n0 = cscale(d0, inv), n1 = cscale(d1, inv);
+  const R is2 = (R)0.70710678118654752440, s2 = (R)1.41421356237309504880;
+  const C t00 = m[0], t11 = m[1], t01 = cscale(m[2], is2);
+  const C v0 = cadd(cmulc(t00, n0), cmulc(t01, n1));
+  const C v1 = cadd(cmulc(t01, n0), cmulc(t11, n1));
+  const C s = cadd(cmulc(v0, n0), cmulc(v1, n1));
+  auto o = [&](C ni, C nj, C vi, C vj) { return csub(cadd(cmul(ni, vj), cmul(vi, nj)), cmul(s, cmul(ni, nj))); };
+  m[0] = o(n0, n0, v0, v0);
+  m[1] = o(n1, n1, v1, v1);
+  m[2] = cscale(o(n0, n1, v0, v1), s2);
+}
+
+// ------------------------------------------------------------ x forward
+// Q voxel rows per block, all ncomp components of each row.  With the
+// tangent mode the damaged isotropic tangent (1-D)(lambda tr(v) 1 + 2 mu v)
+// is applied on load (Eq. (13), secant reading).  Real rows are packed in
+// pairs into one complex FFT (real + i*imag) and separated with the
+// Hermitian symmetry of real-input spectra.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(kXThreads)
+    k_xfwd(const R* __restrict__ in, const uint8_t* __restrict__ phase, const float* __restrict__ dmg,
+           const MatTable<R> mt, Cx<R>* __restrict__ spec, const GridDesc g, const int Q, const AxisPlan px,
+           const Cx<R>* __restrict__ tw) {
+  using C = Cx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int nx = g.nx, nc = g.ncomp, nd = g.ndim;
+  const long long row0 = (long long)blockIdx.x * Q;
+  const int npair = (nc * Q) >> 1;
+  for (int idx = threadIdx.x; idx < Q * nx; idx += blockDim.x) {
+    const int q = idx / nx, x = idx - q * nx;
+    const long long row = row0 + q;
+    R val[6] = {0, 0, 0, 0, 0, 0};
+    if (row < g.nrows) {
+      const long long vox = row * nx + x;
+      for (int c = 0; c < nc; ++c) val[c] = in[c * g.nvox + vox];
+      if (MODE == 1) {
+        const int ph = phase[vox];
+        const R keep = (R)1 - (R)dmg[vox];
+        const R lam = mt.lam[ph] * keep, two_mu = (R)2 * mt.mu[ph] * keep;
+        R tr = 0;
+        for (int i = 0; i < nd; ++i) tr += val[i];
+        for (int c = 0; c < nc; ++c) val[c] = two_mu * val[c] + (c < nd ? lam * tr : (R)0);
+      }
+    }
+    for (int c = 0; c < nc; ++c) {
+      const int rho = q * nc + c;
+      R* slot = reinterpret_cast<R*>(&buf[(rho >> 1) * nx + x]) + (rho & 1);
+      *slot = val[c];
+    }
+  }
+  __syncthreads();
+  fft_lines<kXEpt, false, false>(buf, px, npair, LineMap{1, nx, 0, 1}, tw);
+  const int nxh = g.nxh;
+  for (int idx = threadIdx.x; idx < npair * nxh; idx += blockDim.x) {
+    const int p = idx / nxh, k = idx - p * nxh;
+    const C zk = buf[p * nx + k];
+    const C zm = buf[p * nx + (k == 0 ? 0 : nx - k)];
+    const C xa = C{(zk.x + zm.x) * (R)0.5, (zk.y - zm.y) * (R)0.5};
+    const C xb = C{(zk.y + zm.y) * (R)0.5, (zm.x - zk.x) * (R)0.5};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int rho = 2 * p + h;
+      const int q = rho / nc, c = rho - q * nc;
+      const long long row = row0 + q;
+      if (q < Q && row < g.nrows) spec[(c * g.nrows + row) * nxh + k] = h ? xb : xa;
+    }
+  }
+}
+
+// ------------------------------------------------------------ y columns
+template <typename R, bool INV>
+__global__ void __launch_bounds__(kYThreads)
+    k_ycols(Cx<R>* __restrict__ spec, const GridDesc g, const int TX, const AxisPlan py,
+            const Cx<R>* __restrict__ tw) {
+  using C = Cx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int ny = g.ny, nxh = g.nxh;
+  const int kx0 = blockIdx.x * TX;
+  const int tv = min(TX, nxh - kx0);
+  const long long plane = ((long long)blockIdx.z * g.nz + blockIdx.y) * ny;
+  for (int idx = threadIdx.x; idx < ny * TX; idx += blockDim.x) {
+    const int y = idx / TX, t = idx - y * TX;
+    buf[idx] = t < tv ? spec[(plane + y) * nxh + kx0 + t] : C{0, 0};
+  }
+  __syncthreads();
+  fft_lines<kYEpt, INV, true>(buf, py, TX, LineMap{TX, 0, 1, TX}, tw);
+  for (int idx = threadIdx.x; idx < ny * TX; idx += blockDim.x) {
+    const int y = idx / TX, t = idx - y * TX;
+    if (t < tv) spec[(plane + y) * nxh + kx0 + t] = buf[idx];
+  }
+}
+
+// ------------------------------------------------- z + projection (3D)
+template <typename R>
+__global__ void __launch_bounds__(kZThreads)
+    k_zproj(Cx<R>* __restrict__ spec, const GridDesc g, const int TX, const AxisPlan pz,
+            const Cx<R>* __restrict__ tw, const Cx<R>* __restrict__ gdx, const Cx<R>* __restrict__ gax,
+            const Cx<R>* __restrict__ gdy, const Cx<R>* __restrict__ gay, const Cx<R>* __restrict__ gdz,
+            const Cx<R>* __restrict__ gaz, const unsigned free_mask) {
+  using C = Cx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int nz = g.nz, ny = g.ny, nxh = g.nxh;
+  const int kx0 = blockIdx.x * TX, ky = blockIdx.y;
+  const int tv = min(TX, nxh - kx0);
+  const int plane = nz * TX;
+  for (int idx = threadIdx.x; idx < 6 * plane; idx += blockDim.x) {
+    const int c = idx / plane, rem = idx - c * plane;
+    const int z = rem / TX, t = rem - z * TX;
+    buf[idx] = t < tv ? spec[(((long long)c * nz + z) * ny + ky) * nxh + kx0 + t] : C{0, 0};
+  }
+  __syncthreads();
+  const LineMap lm{TX, plane, 1, TX};
+  fft_lines<kZEpt, false, true>(buf, pz, 6 * TX, lm, tw);
+  const C ay = gay[ky], dy = gdy[ky];
+  for (int pt = threadIdx.x; pt < plane; pt += blockDim.x) {
+    const int z = pt / TX, t = pt - z * TX;
+    const int kx = kx0 + t;
+    if (t >= tv) continue;
+    C m[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) m[c] = buf[c * plane + pt];
+    const C ax = gax[kx], dx = gdx[kx], az = gaz[z], dz = gdz[z];
+    const C d0 = cmul(cmul(dx, ay), az);
+    const C d1 = cmul(cmul(ax, dy), az);
+    const C d2 = cmul(cmul(ax, ay), dz);
+    project3<R>(m, d0, d1, d2, kx == 0 && ky == 0 && z == 0, free_mask);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) buf[c * plane + pt] = m[c];
+  }
+  __syncthreads();
+  fft_lines<kZEpt, true, true>(buf, pz, 6 * TX, lm, tw);
+  for (int idx = threadIdx.x; idx < 6 * plane; idx += blockDim.x) {
+    const int c = idx / plane, rem = idx - c * plane;
+    const int z = rem / TX, t = rem - z * TX;
+    if (t < tv) spec[(((long long)c * nz + z) * ny + ky) * nxh + kx0 + t] = buf[idx];
+  }
+}
+
+// ------------------------------------------------- y + projection (2D)
+template <typename R>
+__global__ void __launch_bounds__(kYThreads)
+    k_yproj2d(Cx<R>* __restrict__ spec, const GridDesc g, const int TX, const AxisPlan py,
+              const Cx<R>* __restrict__ tw, const Cx<R>* __restrict__ gdx, const Cx<R>* __restrict__ gax,
+              const Cx<R>* __restrict__ gdy, const Cx<R>* __restrict__ gay, const unsigned free_mask) {
+  using C = Cx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int ny = g.ny, nxh = g.nxh;
+  const int kx0 = blockIdx.x * TX;
+  const int tv = min(TX, nxh - kx0);
+  const int plane = ny * TX;
+  for (int idx = threadIdx.x; idx < 3 * plane; idx += blockDim.x) {
+    const int c = idx / plane, rem = idx - c * plane;
+    const int y = rem / TX, t = rem - y * TX;
+    buf[idx] = t < tv ? spec[((long long)c * ny + y) * nxh + kx0 + t] : C{0, 0};
+  }
+  __syncthreads();
+  const LineMap lm{TX, plane, 1, TX};
+  fft_lines<kYEpt, false, true>(buf, py, 3 * TX, lm, tw);
+  for (int pt = threadIdx.x; pt < plane; pt += blockDim.x) {
+    const int y = pt / TX, t = pt - y * TX;
+    const int kx = kx0 + t;
+    if (t >= tv) continue;
+    C m[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m[c] = buf[c * plane + pt];
+    const C d0 = cmul(gdx[kx], gay[y]);
+    const C d1 = cmul(gax[kx], gdy[y]);
+    project2<R>(m, d0, d1, kx == 0 && y == 0, free_mask);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) buf[c * plane + pt] = m[c];
+  }
+  __syncthreads();
+  fft_lines<kYEpt, true, true>(buf, py, 3 * TX, lm, tw);
+  for (int idx = threadIdx.x; idx < 3 * plane; idx += blockDim.x) {
+    const int c = idx / plane, rem = idx - c * plane;
+    const int y = rem / TX, t = rem - y * TX;
+    if (t < tv) spec[((long long)c * ny + y) * nxh + kx0 + t] = buf[idx];
+  }
+}
+
+// ------------------------------------------------------------ x inverse
+// Pairs of half spectra are recombined as Z = Xa + i Xb over the full
+// length (Hermitian extension; the imaginary parts of the k = 0 and
+// Nyquist bins are dropped, as for any complex-to-real transform), one
+// inverse complex FFT gives both real rows.  DOT adds sum(out * w) in FP64.
+template <typename R, bool DOT>
+__global__ void __launch_bounds__(kXThreads)
+    k_xinv(const Cx<R>* __restrict__ spec, R* __restrict__ out, const R* __restrict__ dotw,
+           double* __restrict__ partials, const GridDesc g, const int Q, const AxisPlan px,
+           const Cx<R>* __restrict__ tw, const R scale, const bool self_dot) {
+  using C = Cx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  __shared__ double red[32];
+  const int nx = g.nx, nc = g.ncomp, nxh = g.nxh, half = nx >> 1;
+  const long long row0 = (long long)blockIdx.x * Q;
+  const int npair = (nc * Q) >> 1;
+  for (int idx = threadIdx.x; idx < npair * nx; idx += blockDim.x) {
+    const int p = idx / nx, k = idx - p * nx;
+    C xh[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int rho = 2 * p + h;
+      const int q = rho / nc, c = rho - q * nc;
+      const long long row = row0 + q;
+      C x = C{0, 0};
+      if (q < Q && row < g.nrows) {
+        const int kk = k <= half ? k : nx - k;
+        x = spec[(c * g.nrows + row) * nxh + kk];
+        if (kk == 0 || kk == half) x.y = 0;
+        if (k > half) x.y = -x.y;
+      }
+      xh[h] = x;
+    }
+    buf[idx] = C{xh[0].x - xh[1].y, xh[0].y + xh[1].x};
+  }
+  __syncthreads();
+  fft_lines<kXEpt, true, false>(buf, px, npair, LineMap{1, nx, 0, 1}, tw);
+  KSum<R> acc;
+  for (int idx = threadIdx.x; idx < 2 * npair * nx; idx += blockDim.x) {
+    const int rho = idx / nx, x = idx - rho * nx;
+    const int q = rho / nc, c = rho - q * nc;
+    const long long row = row0 + q;
+    if (q < Q && row < g.nrows) {
+      const C z = buf[(rho >> 1) * nx + x];
+      const R val = ((rho & 1) ? z.y : z.x) * scale;
+      const long long off = c * g.nvox + row * nx + x;
+      out[off] = val;
+      if (DOT) acc.add(val * (self_dot ? val : dotw[off]));
+    }
+  }
+  if (DOT) {
+    double v[1] = {acc.value()};
+    block_sum<1>(v, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+  }
+}
+
+// ------------------------------------------------------------ reduction
+__global__ void k_reduce_partials(const double* __restrict__ part, int nb, int ns, double* __restrict__ out) {
+  __shared__ double red[32];
+  const int s = blockIdx.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[(long long)b * ns + s];
+  double v[1] = {acc};
+  block_sum<1>(v, red);
+  if (threadIdx.x == 0) out[s] = v[0];
+}
+
+cudaError_t reduce_partials(const double* part, int nblocks, int ns, double* out, cudaStream_t st,
+                            long long* nlaunch) {
+  k_reduce_partials<<<ns, 256, 0, st>>>(part, nblocks, ns, out);
+  if (nlaunch) ++*nlaunch;
+  return cudaGetLastError();
+}
+
+// ================================================================ host side
+static void make_plan(int n, AxisPlan& p) {
+  p.n = n;
+  p.nstages = 0;
+  int m = n, twos = 0;
+  while (m % 2 == 0) { m /= 2; ++twos; }
+  // powers of two: radix 8 as far as possible, then 4 / 4x4 / 2
+  int n8 = twos / 3, rem = twos % 3;
+  int n4 = 0, n2 = 0;
+  if (rem == 2) n4 = 1;
+  else if (rem == 1) {
+    if (n8 > 0) { --n8; n4 = 2; } else n2 = 1;
+  }
+  for (int i = 0; i < n8; ++i) p.radix[p.nstages++] = 8;
+  for (int i = 0; i < n4; ++i) p.radix[p.nstages++] = 4;
+  for (int i = 0; i < n2; ++i) p.radix[p.nstages++] = 2;
+  while (m % 3 == 0) { m /= 3; p.radix[p.nstages++] = 3; }
+  while (m % 5 == 0) { m /= 5; p.radix[p.nstages++] = 5; }
+}
+
+template <typename R>
+static cudaError_t upload_tables(int n, Cx<R>** tw, Cx<R>** gdiff, Cx<R>** gavg) {
+  std::vector<Cx<R>> t(n), d(n), a(n);
+  for (int k = 0; k < n; ++k) {
+    // angles from long double libm calls, rounded once to R
+    const long double th = 2.0L * 3.14159265358979323846264338327950288L * (long double)k / (long double)n;
+    const long double c = cosl(th), s = sinl(th);
+    t[k] = Cx<R>{(R)c, (R)(-s)};
+    d[k] = (k == 0) ? Cx<R>{0, 0} : Cx<R>{(R)(c - 1.0L), (R)s};
+    a[k] = (2 * k == n) ? Cx<R>{0, 0} : Cx<R>{(R)((1.0L + c) * 0.5L), (R)(s * 0.5L)};
+  }
+  cudaError_t e;
+  if ((e = cudaMalloc(tw, n * sizeof(Cx<R>))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(gdiff, n * sizeof(Cx<R>))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(gavg, n * sizeof(Cx<R>))) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(*tw, t.data(), n * sizeof(Cx<R>), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(*gdiff, d.data(), n * sizeof(Cx<R>), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  return cudaMemcpy(*gavg, a.data(), n * sizeof(Cx<R>), cudaMemcpyHostToDevice);
+}
+
+static int pow2_floor(int v) {
+  int p = 1;
+  while (p * 2 <= v) p *= 2;
+  return p;
+}
+
+template <typename R>
+cudaError_t spectral_setup(const GridDesc& g, SpecWork<R>& w) {
+  using C = Cx<R>;
+  make_plan(g.nx, w.px);
+  make_plan(g.ny, w.py);
+  make_plan(g.ndim == 3 ? g.nz : 1, w.pz);
+  cudaError_t e;
+  const int ns[3] = {g.nx, g.ny, g.nz};
+  for (int a = 0; a < g.ndim; ++a)
+    if ((e = upload_tables<R>(ns[a], &w.tw[a], &w.gdiff[a], &w.gavg[a])) != cudaSuccess) return e;
+  const size_t nspec = (size_t)g.ncomp * g.nrows * g.nxh;
+  if ((e = cudaMalloc(&w.spec, nspec * sizeof(C))) != cudaSuccess) return e;
+  // x passes: npair * nx <= kXThreads * kXEpt complex per block
+  const int ex = kXThreads * kXEpt;
+  int q = (2 * ex) / (g.ncomp * g.nx);
+  if (g.ncomp & 1) q &= ~1;
+  q = std::max(q, (g.ncomp & 1) ? 2 : 1);
+  w.qx = (int)std::min<long long>(q, g.nrows + (g.nrows & 1));
+  // y columns
+  const int ey = kYThreads * kYEpt;
+  w.ty = std::max(1, std::min(pow2_floor(std::max(1, ey / g.ny)), 64));
+  // z + projection (3D) or y + projection (2D)
+  if (g.ndim == 3) {
+    const int ez = std::min(kZThreads * kZEpt, (int)(kSmemCap / sizeof(C)));
+    w.tz = std::max(1, std::min(pow2_floor(std::max(1, ez / (6 * g.nz))), 16));
+  } else {
+    const int e2 = std::min(kYThreads * kYEpt, (int)(kSmemCap / sizeof(C)));
+    w.tz = std::max(1, std::min(pow2_floor(std::max(1, e2 / (3 * g.ny))), 64));
+  }
+  w.max_partials = (int)((g.nrows + w.qx - 1) / w.qx) + 8;
+  w.max_partials = std::max(w.max_partials, 4096 * 8);
+  if ((e = cudaMalloc(&w.partials, (size_t)w.max_partials * sizeof(double))) != cudaSuccess) return e;
+  // opt in to large dynamic shared memory
+  cudaFuncSetAttribute(k_xfwd<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_xfwd<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_ycols<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_ycols<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_zproj<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_yproj2d<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_xinv<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_xinv<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  return cudaGetLastError();
+}
+
+template <typename R>
+void spectral_free(SpecWork<R>& w) {
+  for (int a = 0; a < 3; ++a) {
+    if (w.tw[a]) cudaFree(w.tw[a]);
+    if (w.gdiff[a]) cudaFree(w.gdiff[a]);
+    if (w.gavg[a]) cudaFree(w.gavg[a]);
+    w.tw[a] = w.gdiff[a] = w.gavg[a] = nullptr;
+  }
+  if (w.spec) cudaFree(w.spec);
+  if (w.partials) cudaFree(w.partials);
+  w.spec = nullptr;
+  w.partials = nullptr;
+}
+
+template <typename R>
+cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>& mt, const R* in,
+                           const uint8_t* phase, const float* damage, XIn mode, R* out,
+                           const R* dot_with, double* dot_out, cudaStream_t st, long long* nlaunch) {
+  using C = Cx<R>;
+  long long nl = 0;
+  const int xblocks = (int)((g.nrows + w.qx - 1) / w.qx);
+  const size_t xsm = (size_t)((g.ncomp * w.qx) / 2) * g.nx * sizeof(C);
+  if (mode == XIn::Tangent)
+    k_xfwd<R, 1><<<xblocks, kXThreads, xsm, st>>>(in, phase, damage, mt, w.spec, g, w.qx, w.px, w.tw[0]);
+  else
+    k_xfwd<R, 0><<<xblocks, kXThreads, xsm, st>>>(in, phase, damage, mt, w.spec, g, w.qx, w.px, w.tw[0]);
+  ++nl;
+  if (g.ndim == 3) {
+    const dim3 yg((g.nxh + w.ty - 1) / w.ty, g.nz, g.ncomp);
+    const size_t ysm = (size_t)w.ty * g.ny * sizeof(C);
+    k_ycols<R, false><<<yg, kYThreads, ysm, st>>>(w.spec, g, w.ty, w.py, w.tw[1]);
+    const dim3 zg((g.nxh + w.tz - 1) / w.tz, g.ny);
+    const size_t zsm = (size_t)6 * w.tz * g.nz * sizeof(C);
+    k_zproj<R><<<zg, kZThreads, zsm, st>>>(w.spec, g, w.tz, w.pz, w.tw[2], w.gdiff[0], w.gavg[0], w.gdiff[1],
+                                           w.gavg[1], w.gdiff[2], w.gavg[2], w.free_mask);
+    k_ycols<R, true><<<yg, kYThreads, ysm, st>>>(w.spec, g, w.ty, w.py, w.tw[1]);
+    nl += 3;
+  } else {
+    const dim3 pg((g.nxh + w.tz - 1) / w.tz);
+    const size_t psm = (size_t)3 * w.tz * g.ny * sizeof(C);
+    k_yproj2d<R><<<pg, kYThreads, psm, st>>>(w.spec, g, w.tz, w.py, w.tw[1], w.gdiff[0], w.gavg[0], w.gdiff[1],
+                                             w.gavg[1], w.free_mask);
+    ++nl;
+  }
+  const R scale = (R)(1.0 / (double)g.nvox);
+  if (dot_with) {
+    const bool self = (dot_with == out);
+    k_xinv<R, true><<<xblocks, kXThreads, xsm, st>>>(w.spec, out, self ? nullptr : dot_with, w.partials, g, w.qx,
+                                                     w.px, w.tw[0], scale, self);
+    ++nl;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = reduce_partials(w.partials, xblocks, 1, dot_out, st, &nl);
+    if (nlaunch) *nlaunch += nl;
+    return e;
+  }
+  k_xinv<R, false><<<xblocks, kXThreads, xsm, st>>>(w.spec, out, nullptr, nullptr, g, w.qx, w.px, w.tw[0], scale,
+                                                    false);
+  ++nl;
+  if (nlaunch) *nlaunch += nl;
+  return cudaGetLastError();
+}
+
+template cudaError_t spectral_setup<float>(const GridDesc&, SpecWork<float>&);
+template cudaError_t spectral_setup<double>(const GridDesc&, SpecWork<double>&);
+template void spectral_free<float>(SpecWork<float>&);
+template void spectral_free<double>(SpecWork<double>&);
+template cudaError_t spectral_apply<float>(const GridDesc&, SpecWork<float>&, const MatTable<float>&, const float*,
+                                           const uint8_t*, const float*, XIn, float*, const float*, double*,
+                                           cudaStream_t, long long*);
+template cudaError_t spectral_apply<double>(const GridDesc&, SpecWork<double>&, const MatTable<double>&,
+                                            const double*, const uint8_t*, const float*, XIn, double*,
+                                            const double*, double*, cudaStream_t, long long*);
+
+}  // namespace rve

@@ -1,0 +1,52 @@
+// Host-side description of the FFT / projection passes of one grid.
+#pragma once
+
+#include "common.cuh"
+
+namespace rve {
+
+struct GridDesc {
+  int ndim;       // 2 or 3
+  int nx, ny, nz; // nz = 1 in 2D
+  int nxh;        // nx/2 + 1 (half spectrum along x)
+  int ncomp;      // 3 or 6
+  long long nvox;
+  long long nrows;  // ny * nz voxel rows along x
+};
+
+// Tables and workspace for the spectral passes at precision R.
+template <typename R> struct SpecWork {
+  AxisPlan px, py, pz;
+  Cx<R>* tw[3] = {nullptr, nullptr, nullptr};    // e^{-2 pi i t / n_axis}
+  Cx<R>* gdiff[3] = {nullptr, nullptr, nullptr}; // e^{i th} - 1 (exact 0 at k=0)
+  Cx<R>* gavg[3] = {nullptr, nullptr, nullptr};  // (1 + e^{i th})/2 (exact 0 at 2k=n)
+  Cx<R>* spec = nullptr;                          // ncomp * nz * ny * nxh
+  unsigned free_mask = 0;                         // bit c: Mandel comp c stress-controlled
+  // tiling
+  int qx;   // voxel rows per x-pass block
+  int ty;   // kx columns per y-pass block
+  int tz;   // kx columns per z-pass / 2D y-pass block
+  double* partials = nullptr;  // per-block FP64 partial sums (epilogues)
+  int max_partials = 0;
+};
+
+enum class XIn { Plain = 0, Tangent = 1 };
+
+// Launch helpers (hv_passes.cu).  Every pass runs on `st`; the number of
+// launches issued is added to *nlaunch.
+template <typename R>
+cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>& mt, const R* in,
+                           const uint8_t* phase, const float* damage, XIn mode, R* out,
+                           const R* dot_with, double* dot_out, cudaStream_t st, long long* nlaunch);
+
+template <typename R>
+cudaError_t spectral_setup(const GridDesc& g, SpecWork<R>& w);
+template <typename R>
+void spectral_free(SpecWork<R>& w);
+
+// FP64 final reduction of per-block partials: out[s] = sum_b part[b*ns + s]
+// (out: ns contiguous device doubles).  Fixed summation order.
+cudaError_t reduce_partials(const double* part, int nblocks, int ns, double* out, cudaStream_t st,
+                            long long* nlaunch);
+
+}  // namespace rve

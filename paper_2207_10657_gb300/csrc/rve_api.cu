@@ -1,0 +1,500 @@
+// C ABI: context management, the Hessian-vector product entry points and
+// the trust-region Newton / Steihaug-CG load step (Algorithms 1 and 2).
+// The control loop runs on the host; every arithmetic step (fields and
+// FP64 scalars) runs in the kernels of hv_passes.cu and solver_kernels.cu,
+// and the host only reads back the small scalar block to branch.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/rve.h"
+#include "hv_passes.cuh"
+#include "solver_kernels.cuh"
+
+using namespace rve;
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+__global__ void k_set_cg_params(DevScalars* S, double R, double eta_cg, double thr, int max_cg, double eta_up,
+                                double Rmax) {
+  S->R = R;
+  S->tol = eta_cg * sqrt(S->gg);
+  S->thr = thr;
+  S->max_cg = max_cg;
+  S->eta_up = eta_up;
+  S->Rmax = Rmax;
+}
+
+__global__ void k_energy_s(DevScalars* S) {
+  S->dm = S->sp + 0.5 * S->pBp;
+  S->dW = 0.5 * (S->sp + S->stp);
+}
+
+template <typename R>
+struct Impl {
+  SpecWork<R> sw;
+  MatTable<R> mt;
+  uint8_t* phase = nullptr;
+  R *eps = nullptr, *sig = nullptr, *sig_t = nullptr, *g = nullptr, *z = nullptr, *r = nullptr, *d = nullptr,
+    *Hd = nullptr, *tmp = nullptr;
+  float *D = nullptr, *D_t = nullptr, *kap = nullptr, *kap_t = nullptr, *khist = nullptr;
+  DevScalars* S = nullptr;
+};
+
+bool five_smooth_even(int n) {
+  if (n < 2 || n > 1024 || (n & 1)) return false;
+  int m = n;
+  for (int p : {2, 3, 5})
+    while (m % p == 0) m /= p;
+  return m == 1;
+}
+
+}  // namespace
+
+struct rve_ctx {
+  int precision = 32;
+  GridDesc g{};
+  cudaStream_t st = nullptr;
+  std::string err = "no error";
+  long long hv = 0, launches = 0;
+  rve_solver_opts opts{};
+  bool radius_set = false;
+  double R = 0.0, Rmax = 0.0;
+  unsigned free_mask = 0;
+  DevScalars* Sh = nullptr;  // pinned host mirror
+  void* impl = nullptr;
+};
+
+namespace {
+
+rve_status fail(rve_ctx* c, rve_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+rve_status cuda_fail(rve_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(c, e == cudaErrorMemoryAllocation ? RVE_ERR_OOM : RVE_ERR_CUDA, m);
+}
+
+#define CK(call, where)                                  \
+  do {                                                   \
+    cudaError_t e__ = (call);                            \
+    if (e__ != cudaSuccess) return cuda_fail(c, e__, where); \
+  } while (0)
+
+template <typename R>
+Impl<R>* impl_of(rve_ctx* c) {
+  return static_cast<Impl<R>*>(c->impl);
+}
+
+template <typename R>
+void impl_free(Impl<R>* m) {
+  if (!m) return;
+  spectral_free(m->sw);
+  void* ptrs[] = {m->phase, m->eps, m->sig, m->sig_t, m->g, m->z, m->r, m->d, m->Hd, m->tmp,
+                  m->D, m->D_t, m->kap, m->kap_t, m->khist, m->S};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete m;
+}
+
+template <typename R>
+rve_status read_scalars(rve_ctx* c) {
+  Impl<R>* m = impl_of<R>(c);
+  CK(cudaMemcpyAsync(c->Sh, m->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->st), "read scalars");
+  CK(cudaStreamSynchronize(c->st), "synchronize");
+  return RVE_OK;
+}
+
+template <typename R>
+rve_status create_impl(rve_ctx* c, const uint8_t* phase_ids, const rve_phase* phases, int nphase) {
+  Impl<R>* m = new (std::nothrow) Impl<R>();
+  if (!m) return fail(c, RVE_ERR_OOM, "host allocation failed");
+  c->impl = m;
+  const GridDesc& g = c->g;
+  m->mt.nphase = nphase;
+  for (int i = 0; i < kMaxPhases; ++i) {
+    m->mt.lam[i] = m->mt.mu[i] = 0;
+    m->mt.kappa0[i] = m->mt.kappaf[i] = 0.f;
+    m->mt.damaging[i] = 0;
+  }
+  for (int i = 0; i < nphase; ++i) {
+    const double E = phases[i].E, nu = phases[i].nu;
+    m->mt.lam[i] = (R)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
+    m->mt.mu[i] = (R)(E / (2.0 * (1.0 + nu)));
+    m->mt.damaging[i] = phases[i].damaging ? 1 : 0;
+    m->mt.kappa0[i] = (float)phases[i].kappa0;
+    m->mt.kappaf[i] = (float)phases[i].kappaf;
+  }
+  CK(spectral_setup<R>(g, m->sw), "spectral setup");
+  const size_t nf = (size_t)g.ncomp * g.nvox * sizeof(R);
+  const size_t ns = (size_t)g.nvox * sizeof(float);
+  R** fields[] = {&m->eps, &m->sig, &m->sig_t, &m->g, &m->z, &m->r, &m->d, &m->Hd, &m->tmp};
+  for (R** f : fields) CK(cudaMalloc(f, nf), "field allocation");
+  float** sf[] = {&m->D, &m->D_t, &m->kap, &m->kap_t, &m->khist};
+  for (float** f : sf) CK(cudaMalloc(f, ns), "scalar-field allocation");
+  CK(cudaMalloc(&m->phase, g.nvox), "phase allocation");
+  CK(cudaMalloc(&m->S, sizeof(DevScalars)), "scalar allocation");
+  CK(cudaMemsetAsync(m->S, 0, sizeof(DevScalars), c->st), "memset");
+  CK(cudaMemcpyAsync(m->phase, phase_ids, g.nvox, cudaMemcpyDeviceToDevice, c->st), "phase copy");
+  // validate ids once
+  std::vector<uint8_t> ids(g.nvox);
+  CK(cudaMemcpyAsync(ids.data(), m->phase, g.nvox, cudaMemcpyDeviceToHost, c->st), "phase check copy");
+  CK(cudaStreamSynchronize(c->st), "synchronize");
+  for (long long i = 0; i < g.nvox; ++i)
+    if (ids[i] >= nphase) return fail(c, RVE_ERR_ARG, "phase id out of range at voxel " + std::to_string(i));
+  CK(cudaMemsetAsync(m->eps, 0, nf, c->st), "memset");
+  CK(cudaMemsetAsync(m->khist, 0, ns, c->st), "memset");
+  CK(cudaMemsetAsync(m->kap, 0, ns, c->st), "memset");
+  // state eps = 0: sigma = 0, D = 0
+  CK(trial_eval<R>(g, m->mt, m->phase, m->eps, nullptr, m->khist, nullptr, nullptr, m->sig, m->D, m->kap, m->S,
+                   m->sw.partials, c->st, &c->launches),
+     "initial state");
+  CK(cudaStreamSynchronize(c->st), "synchronize");
+  return RVE_OK;
+}
+
+// Steihaug CG on H p = -g inside radius S.R (Algorithm 1).  Result in z,
+// exit status in S.status.
+template <typename R>
+rve_status steihaug(rve_ctx* c, rve_step_report* rep) {
+  Impl<R>* m = impl_of<R>(c);
+  const GridDesc& g = c->g;
+  long long* nl = &c->launches;
+  k_set_cg_params<<<1, 1, 0, c->st>>>(m->S, c->R, c->opts.eta_cg, c->opts.restart_thr, c->opts.max_cg,
+                                      c->opts.eta_up, c->Rmax);
+  ++*nl;
+  CK(cg_init<R>(g, m->g, m->z, m->r, m->d, m->S, m->sw.partials, c->st, nl), "cg init");
+  rve_status s = read_scalars<R>(c);
+  if (s != RVE_OK) return s;
+  if (c->Sh->status != CG_RUN) return RVE_OK;
+  for (;;) {
+    CK(spectral_apply<R>(g, m->sw, m->mt, m->d, m->phase, m->D, XIn::Tangent, m->Hd, m->d, &m->S->dHd, c->st, nl),
+       "hessp");
+    ++c->hv;
+    if (rep) ++rep->hv_products;
+    CK(cg_alpha(m->S, c->st, nl), "cg alpha");
+    CK(cg_update<R>(g, m->z, m->r, m->d, m->Hd, m->S, m->sw.partials, c->st, nl), "cg update");
+    CK(cg_beta(m->S, c->st, nl), "cg beta");
+    s = read_scalars<R>(c);
+    if (s != RVE_OK) return s;
+    if (c->Sh->status != CG_RUN) break;
+    if (c->Sh->restart) {
+      CK(spectral_apply<R>(g, m->sw, m->mt, m->z, m->phase, m->D, XIn::Tangent, m->tmp, nullptr, nullptr, c->st, nl),
+         "hessp (restart)");
+      ++c->hv;
+      if (rep) ++rep->hv_products;
+      CK(cg_restart<R>(g, m->r, m->tmp, m->g, m->S, m->sw.partials, c->st, nl), "cg restart");
+    }
+    CK(cg_dupdate<R>(g, m->z, m->r, m->d, m->S, m->sw.partials, c->st, nl), "cg direction");
+  }
+  if (rep) {
+    rep->cg_iters += c->Sh->iters;
+    rep->restarts += c->Sh->restarts;
+  }
+  if (c->Sh->status == CG_NONFINITE) return fail(c, RVE_ERR_NONFINITE, "non-finite value in CG");
+  return RVE_OK;
+}
+
+// gradient g = G : sigma with |g|^2 into S.gg
+template <typename R>
+rve_status gradient(rve_ctx* c) {
+  Impl<R>* m = impl_of<R>(c);
+  CK(spectral_apply<R>(c->g, m->sw, m->mt, m->sig, m->phase, m->D, XIn::Plain, m->g, m->g, &m->S->gg, c->st,
+                       &c->launches),
+     "gradient");
+  return RVE_OK;
+}
+
+template <typename R>
+rve_status solve_step_impl(rve_ctx* c, const double dE[6], const void* init, rve_step_report* rep) {
+  Impl<R>* m = impl_of<R>(c);
+  const GridDesc& g = c->g;
+  long long* nl = &c->launches;
+  rve_step_report local{};
+  rve_step_report* rp = rep ? rep : &local;
+  std::memset(rp, 0, sizeof(*rp));
+  if (!c->radius_set) {
+    double n2 = 0;
+    for (int i = 0; i < g.ncomp; ++i) n2 += dE[i] * dE[i];
+    const double def = 10.0 * std::sqrt((double)g.nvox) * std::sqrt(n2);
+    c->R = c->opts.R0 > 0 ? c->opts.R0 : def;
+    c->Rmax = c->opts.Rmax > 0 ? c->opts.Rmax : std::max(c->R, def);
+    if (!(c->R > 0)) c->R = c->Rmax = 1.0;
+    c->radius_set = true;
+  }
+  CK(add_uniform<R>(g, m->eps, dE, c->st, nl), "load increment");
+  if (init) {
+    CK(spectral_apply<R>(g, m->sw, m->mt, (const R*)init, m->phase, m->D, XIn::Plain, m->tmp, nullptr, nullptr,
+                         c->st, nl),
+       "warm start projection");
+    CK(axpy<R>((long long)g.ncomp * g.nvox, (R)1, m->tmp, m->eps, c->st, nl), "warm start add");
+  }
+  CK(trial_eval<R>(g, m->mt, m->phase, m->eps, nullptr, m->khist, nullptr, nullptr, m->sig, m->D, m->kap, m->S,
+                   m->sw.partials, c->st, nl),
+     "stress");
+  rve_status s = gradient<R>(c);
+  if (s != RVE_OK) return s;
+  if ((s = read_scalars<R>(c)) != RVE_OK) return s;
+  double rel = c->Sh->sts > 0 ? std::sqrt(c->Sh->gg / c->Sh->sts) : 0.0;
+  bool converged = rel <= c->opts.eta_eq;
+  while (!converged && rp->nr_iters < c->opts.max_nr) {
+    rp->nr_iters++;
+    if ((s = steihaug<R>(c, rp)) != RVE_OK) return s;
+    CK(trial_eval<R>(g, m->mt, m->phase, m->eps, m->z, m->khist, m->sig, m->D, m->sig_t, m->D_t, m->kap_t, m->S,
+                     m->sw.partials, c->st, nl),
+       "trial stress");
+    CK(tr_decide(m->S, c->st, nl), "ratio test");
+    if ((s = read_scalars<R>(c)) != RVE_OK) return s;
+    if (c->Sh->nonfinite) return fail(c, RVE_ERR_NONFINITE, "non-finite trial state");
+    c->R = c->Sh->R;
+    if (c->Sh->on_boundary) rp->boundary_hits++;
+    if (!c->Sh->accept) {
+      rp->rejected++;
+      continue;
+    }
+    const bool on_b = c->Sh->on_boundary;
+    const double pp = c->Sh->pp, ee = c->Sh->ee, sts = c->Sh->sts;
+    CK(axpy<R>((long long)g.ncomp * g.nvox, (R)1, m->z, m->eps, c->st, nl), "accept step");
+    std::swap(m->sig, m->sig_t);
+    std::swap(m->D, m->D_t);
+    std::swap(m->kap, m->kap_t);
+    if ((s = gradient<R>(c)) != RVE_OK) return s;
+    if ((s = read_scalars<R>(c)) != RVE_OK) return s;
+    rel = sts > 0 ? std::sqrt(c->Sh->gg / sts) : 0.0;
+    const double rnr = ee > 0 ? std::sqrt(pp / ee) : 0.0;
+    if (!on_b && (rel <= c->opts.eta_eq || (c->opts.eta_nr > 0 && rnr <= c->opts.eta_nr))) converged = true;
+  }
+  CK(field_means<R>(g, m->sig, m->eps, m->S, m->sw.partials, c->st, nl), "means");
+  if ((s = read_scalars<R>(c)) != RVE_OK) return s;
+  for (int i = 0; i < 6; ++i) {
+    rp->mean_stress[i] = c->Sh->msig[i] / (double)g.nvox;
+    rp->mean_strain[i] = c->Sh->meps[i] / (double)g.nvox;
+  }
+  rp->rel_residual = rel;
+  rp->R = c->R;
+  rp->converged = converged ? 1 : 0;
+  if (!converged) return fail(c, RVE_ERR_NOT_CONVERGED, "load step did not converge within max_nr");
+  // commit history: kappa_n <- max(kappa_n, kappa(eps)) (kap already holds the max)
+  CK(cudaMemcpyAsync(m->khist, m->kap, (size_t)g.nvox * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "commit");
+  CK(cudaStreamSynchronize(c->st), "synchronize");
+  return RVE_OK;
+}
+
+template <typename R>
+rve_status set_state_impl(rve_ctx* c, const void* strain, const float* khist) {
+  Impl<R>* m = impl_of<R>(c);
+  const GridDesc& g = c->g;
+  CK(cudaMemcpyAsync(m->eps, strain, (size_t)g.ncomp * g.nvox * sizeof(R), cudaMemcpyDeviceToDevice, c->st),
+     "state copy");
+  if (khist)
+    CK(cudaMemcpyAsync(m->khist, khist, (size_t)g.nvox * sizeof(float), cudaMemcpyDeviceToDevice, c->st),
+       "history copy");
+  else
+    CK(cudaMemsetAsync(m->khist, 0, (size_t)g.nvox * sizeof(float), c->st), "history reset");
+  CK(trial_eval<R>(g, m->mt, m->phase, m->eps, nullptr, m->khist, nullptr, nullptr, m->sig, m->D, m->kap, m->S,
+                   m->sw.partials, c->st, &c->launches),
+     "state stress");
+  return RVE_OK;
+}
+
+template <typename R>
+rve_status get_state_impl(rve_ctx* c, void* strain, float* kappa, void* stress, float* damage) {
+  Impl<R>* m = impl_of<R>(c);
+  const GridDesc& g = c->g;
+  const size_t nf = (size_t)g.ncomp * g.nvox * sizeof(R), ns = (size_t)g.nvox * sizeof(float);
+  if (strain) CK(cudaMemcpyAsync(strain, m->eps, nf, cudaMemcpyDeviceToDevice, c->st), "copy");
+  if (stress) CK(cudaMemcpyAsync(stress, m->sig, nf, cudaMemcpyDeviceToDevice, c->st), "copy");
+  if (kappa) CK(cudaMemcpyAsync(kappa, m->khist, ns, cudaMemcpyDeviceToDevice, c->st), "copy");
+  if (damage) CK(cudaMemcpyAsync(damage, m->D, ns, cudaMemcpyDeviceToDevice, c->st), "copy");
+  return RVE_OK;
+}
+
+template <typename R>
+rve_status energy_grad_impl(rve_ctx* c, const void* p, double* dW, double* dm, void* grad) {
+  Impl<R>* m = impl_of<R>(c);
+  const GridDesc& g = c->g;
+  CK(trial_eval<R>(g, m->mt, m->phase, m->eps, (const R*)p, m->khist, m->sig, m->D, m->sig_t, m->D_t, m->kap_t,
+                   m->S, m->sw.partials, c->st, &c->launches),
+     "trial stress");
+  k_energy_s<<<1, 1, 0, c->st>>>(m->S);
+  ++c->launches;
+  if (grad)
+    CK(spectral_apply<R>(g, m->sw, m->mt, m->sig_t, m->phase, m->D, XIn::Plain, (R*)grad, nullptr, nullptr, c->st,
+                         &c->launches),
+       "gradient");
+  rve_status s = read_scalars<R>(c);
+  if (s != RVE_OK) return s;
+  if (dW) *dW = c->Sh->dW;
+  if (dm) *dm = c->Sh->dm;
+  return RVE_OK;
+}
+
+template <typename R>
+rve_status apply_impl(rve_ctx* c, const void* v, void* out, bool tangent) {
+  Impl<R>* m = impl_of<R>(c);
+  CK(spectral_apply<R>(c->g, m->sw, m->mt, (const R*)v, m->phase, m->D, tangent ? XIn::Tangent : XIn::Plain,
+                       (R*)out, nullptr, nullptr, c->st, &c->launches),
+     tangent ? "hessp" : "project");
+  if (tangent) ++c->hv;
+  return RVE_OK;
+}
+
+}  // namespace
+
+// ============================================================ C ABI
+extern "C" {
+
+void rve_default_opts(rve_solver_opts* o) {
+  if (!o) return;
+  o->eta_eq = 1e-6;
+  o->eta_nr = 0.0;
+  o->eta_cg = 1e-2;
+  o->eta_up = 0.1;
+  o->R0 = 0.0;
+  o->Rmax = 0.0;
+  o->max_nr = 50;
+  o->max_cg = 1000;
+  o->restart_thr = 0.2;
+  o->precision = 32;
+}
+
+rve_status rve_create(const int dims[3], int ndim, const uint8_t* phase_ids_dev, const rve_phase* phases, int nphase,
+                      const rve_solver_opts* opts, void* stream, rve_t* out) {
+  if (!out) return fail(nullptr, RVE_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!dims || !phase_ids_dev || !phases) return fail(nullptr, RVE_ERR_ARG, "NULL argument");
+  if (ndim != 2 && ndim != 3) return fail(nullptr, RVE_ERR_ARG, "ndim must be 2 or 3");
+  for (int a = 0; a < ndim; ++a)
+    if (!five_smooth_even(dims[a]))
+      return fail(nullptr, RVE_ERR_ARG, "every dim must be even, in [2, 1024], with prime factors 2, 3, 5 only");
+  if (nphase < 1 || nphase > kMaxPhases) return fail(nullptr, RVE_ERR_ARG, "nphase must be in [1, 16]");
+  for (int i = 0; i < nphase; ++i) {
+    const rve_phase& p = phases[i];
+    if (!(p.E > 0) || !(p.nu > -1.0 && p.nu < 0.5)) return fail(nullptr, RVE_ERR_ARG, "invalid elastic constants");
+    if (p.damaging && !(p.kappa0 > 0 && p.kappaf > p.kappa0))
+      return fail(nullptr, RVE_ERR_ARG, "damaging phase needs 0 < kappa0 < kappaf");
+  }
+  rve_ctx* c = new (std::nothrow) rve_ctx();
+  if (!c) return fail(nullptr, RVE_ERR_OOM, "host allocation failed");
+  if (opts) c->opts = *opts;
+  else rve_default_opts(&c->opts);
+  if (c->opts.precision != 32 && c->opts.precision != 64) {
+    delete c;
+    return fail(nullptr, RVE_ERR_ARG, "precision must be 32 or 64");
+  }
+  if (c->opts.max_nr < 1 || c->opts.max_cg < 1) {
+    delete c;
+    return fail(nullptr, RVE_ERR_ARG, "max_nr and max_cg must be >= 1");
+  }
+  c->precision = c->opts.precision;
+  c->st = static_cast<cudaStream_t>(stream);
+  GridDesc& g = c->g;
+  g.ndim = ndim;
+  g.nx = dims[0];
+  g.ny = dims[1];
+  g.nz = ndim == 3 ? dims[2] : 1;
+  g.nxh = g.nx / 2 + 1;
+  g.ncomp = ndim == 3 ? 6 : 3;
+  g.nvox = (long long)g.nx * g.ny * g.nz;
+  g.nrows = (long long)g.ny * g.nz;
+  cudaError_t e = cudaMallocHost(&c->Sh, sizeof(DevScalars));
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(nullptr, RVE_ERR_OOM, "pinned allocation failed");
+  }
+  rve_status s = c->precision == 32 ? create_impl<float>(c, phase_ids_dev, phases, nphase)
+                                    : create_impl<double>(c, phase_ids_dev, phases, nphase);
+  if (s != RVE_OK) {
+    g_create_error = c->err;
+    rve_destroy(c);
+    return s;
+  }
+  *out = c;
+  return RVE_OK;
+}
+
+#define DISPATCH(c, fn, ...) ((c)->precision == 32 ? fn<float>(c, __VA_ARGS__) : fn<double>(c, __VA_ARGS__))
+
+rve_status rve_set_state(rve_t c, const void* strain, const float* khist) {
+  if (!c) return RVE_ERR_ARG;
+  if (!strain) return fail(c, RVE_ERR_ARG, "strain is NULL");
+  return DISPATCH(c, set_state_impl, strain, khist);
+}
+
+rve_status rve_get_state(rve_t c, void* strain, float* kappa, void* stress, float* damage) {
+  if (!c) return RVE_ERR_ARG;
+  return DISPATCH(c, get_state_impl, strain, kappa, stress, damage);
+}
+
+rve_status rve_set_damage(rve_t c, const float* damage) {
+  if (!c) return RVE_ERR_ARG;
+  if (!damage) return fail(c, RVE_ERR_ARG, "damage is NULL");
+  float* D = c->precision == 32 ? impl_of<float>(c)->D : impl_of<double>(c)->D;
+  CK(cudaMemcpyAsync(D, damage, (size_t)c->g.nvox * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "damage copy");
+  return RVE_OK;
+}
+
+rve_status rve_set_free_mask(rve_t c, const uint8_t fm[6]) {
+  if (!c) return RVE_ERR_ARG;
+  if (!fm) return fail(c, RVE_ERR_ARG, "free_mask is NULL");
+  unsigned bits = 0;
+  for (int i = 0; i < c->g.ncomp; ++i)
+    if (fm[i]) bits |= 1u << i;
+  c->free_mask = bits;
+  if (c->precision == 32) impl_of<float>(c)->sw.free_mask = bits;
+  else impl_of<double>(c)->sw.free_mask = bits;
+  return RVE_OK;
+}
+
+rve_status rve_hessp(rve_t c, const void* v, void* out) {
+  if (!c) return RVE_ERR_ARG;
+  if (!v || !out) return fail(c, RVE_ERR_ARG, "NULL field");
+  return DISPATCH(c, apply_impl, v, out, true);
+}
+
+rve_status rve_project(rve_t c, const void* v, void* out) {
+  if (!c) return RVE_ERR_ARG;
+  if (!v || !out) return fail(c, RVE_ERR_ARG, "NULL field");
+  return DISPATCH(c, apply_impl, v, out, false);
+}
+
+rve_status rve_energy_grad(rve_t c, const void* p, double* dW, double* dm, void* grad) {
+  if (!c) return RVE_ERR_ARG;
+  return DISPATCH(c, energy_grad_impl, p, dW, dm, grad);
+}
+
+rve_status rve_solve_step(rve_t c, const double dE[6], const uint8_t fm[6], const void* init, rve_step_report* rep) {
+  if (!c) return RVE_ERR_ARG;
+  if (!dE) return fail(c, RVE_ERR_ARG, "dE is NULL");
+  if (fm) {
+    rve_status s = rve_set_free_mask(c, fm);
+    if (s != RVE_OK) return s;
+  }
+  return DISPATCH(c, solve_step_impl, dE, init, rep);
+}
+
+const char* rve_last_error(rve_t c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+long long rve_hv_count(rve_t c) { return c ? c->hv : 0; }
+long long rve_launch_count(rve_t c) { return c ? c->launches : 0; }
+
+void rve_destroy(rve_t c) {
+  if (!c) return;
+  if (c->impl) {
+    if (c->precision == 32) impl_free(impl_of<float>(c));
+    else impl_free(impl_of<double>(c));
+  }
+  if (c->Sh) cudaFreeHost(c->Sh);
+  delete c;
+}
+
+}  // extern "C"

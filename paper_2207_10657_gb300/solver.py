@@ -1,0 +1,141 @@
+"""PyTorch-facing wrapper over the C ABI: tensors in, tensors out.
+
+Torch provides device memory and the CUDA stream; all arithmetic runs in
+librve.so.  Shapes follow the library layout: a field is (ncomp, Nz, Ny, Nx)
+in 3D or (ncomp, Ny, Nx) in 2D, Mandel components, C-contiguous.
+"""
+from dataclasses import dataclass
+
+import torch
+
+from . import binding as B
+
+
+@dataclass
+class Phase:
+    """One material phase (Appendix A): isotropic E, nu; optional damage with
+    the bilinear law between kappa0 and kappaf."""
+    E: float
+    nu: float
+    damaging: bool = False
+    kappa0: float = 0.0
+    kappaf: float = 0.0
+
+    def as_tuple(self):
+        return (float(self.E), float(self.nu), 1 if self.damaging else 0, float(self.kappa0), float(self.kappaf))
+
+
+def make_opts(precision=32, **kw):
+    o = B.rve_default_opts()
+    o.precision = int(precision)
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _report_dict(rep):
+    return {
+        "nr_iters": rep.nr_iters, "cg_iters": rep.cg_iters, "hv_products": rep.hv_products,
+        "restarts": rep.restarts, "rejected": rep.rejected, "boundary_hits": rep.boundary_hits,
+        "converged": bool(rep.converged), "rel_residual": rep.rel_residual, "R": rep.R,
+        "mean_stress": list(rep.mean_stress), "mean_strain": list(rep.mean_strain),
+    }
+
+
+class RVESolver:
+    def __init__(self, dims, phase_ids, phases, precision=32, stream=None, **opts):
+        if not torch.cuda.is_available():
+            raise RuntimeError("RVESolver needs a CUDA device (there is no CPU path)")
+        self.dims = tuple(int(d) for d in dims)
+        self.ndim = len(self.dims)
+        self.ncomp = 3 if self.ndim == 2 else 6
+        self.shape = tuple(reversed(self.dims))
+        self.dtype = torch.float32 if precision == 32 else torch.float64
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        ids = torch.as_tensor(phase_ids, dtype=torch.uint8).to(self.device).contiguous()
+        if tuple(ids.shape) != self.shape:
+            raise ValueError(f"phase_ids shape {tuple(ids.shape)} != grid {self.shape}")
+        self._ids = ids
+        self.phases = [p if isinstance(p, Phase) else Phase(*p) for p in phases]
+        self.opts = make_opts(precision, **opts)
+        self.h = B.rve_create(self.dims, self.ndim, ids.data_ptr(), [p.as_tuple() for p in self.phases],
+                              self.opts, self.stream.cuda_stream)
+
+    # ------------------------------------------------------------ helpers
+    def field(self, fill=None):
+        t = torch.empty((self.ncomp,) + self.shape, dtype=self.dtype, device=self.device)
+        if fill is not None:
+            t.fill_(fill)
+        return t
+
+    def scalar_field(self):
+        return torch.empty(self.shape, dtype=torch.float32, device=self.device)
+
+    def _chk(self, t, kind="field"):
+        want = (self.ncomp,) + self.shape if kind == "field" else self.shape
+        dt = self.dtype if kind == "field" else torch.float32
+        if t.device != self.device or t.dtype != dt or tuple(t.shape) != want or not t.is_contiguous():
+            raise ValueError(f"expected contiguous {dt} {kind} of shape {want} on {self.device}, "
+                             f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+        return t.data_ptr()
+
+    # ------------------------------------------------------------ API
+    def hessp(self, v, out=None):
+        out = self.field() if out is None else out
+        B.rve_hessp(self.h, self._chk(v), self._chk(out))
+        return out
+
+    def project(self, v, out=None):
+        out = self.field() if out is None else out
+        B.rve_project(self.h, self._chk(v), self._chk(out))
+        return out
+
+    def set_state(self, eps, kappa=None):
+        B.rve_set_state(self.h, self._chk(eps), self._chk(kappa, "scalar") if kappa is not None else 0)
+
+    def get_state(self):
+        eps, sig = self.field(), self.field()
+        kap, dmg = self.scalar_field(), self.scalar_field()
+        B.rve_get_state(self.h, eps.data_ptr(), kap.data_ptr(), sig.data_ptr(), dmg.data_ptr())
+        return {"eps": eps, "sigma": sig, "kappa": kap, "damage": dmg}
+
+    def set_damage(self, D):
+        B.rve_set_damage(self.h, self._chk(D, "scalar"))
+
+    def set_free_mask(self, mask):
+        B.rve_set_free_mask(self.h, mask)
+
+    def energy_grad(self, p=None, want_grad=True):
+        grad = self.field() if want_grad else None
+        dW, dm = B.rve_energy_grad(self.h, self._chk(p) if p is not None else 0,
+                                   grad.data_ptr() if grad is not None else 0)
+        return dW, dm, grad
+
+    def solve_step(self, dE, free_mask=None, init=None, raise_on_error=True):
+        st, rep = B.rve_solve_step(self.h, dE, free_mask, self._chk(init) if init is not None else 0,
+                                   raise_on_error)
+        d = _report_dict(rep)
+        d["status"] = st
+        return d
+
+    @property
+    def hv_count(self):
+        return B.rve_hv_count(self.h)
+
+    @property
+    def launch_count(self):
+        return B.rve_launch_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            B.rve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

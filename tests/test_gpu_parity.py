@@ -1,0 +1,246 @@
+"""GPU path vs the FP64 CPU oracle, element by element (needs a GB300).
+
+Tolerances: FP64 fields agree to 1e-11 relative (rounding of different
+summation orders over O(log N) FFT stages); FP32 fields to 2e-6 relative L2
+for single products (about 10x the FP32 unit roundoff times the FFT depth).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import random_spheres, circular_inclusion, damage_snapshot, random_field, laminate
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+MATRIX = (1.0, 0.3, True, 1e-4, 1e-3)
+STIFF = (10.0, 0.2, False, 0.0, 0.0)
+TOL = {32: 2e-6, 64: 1e-11}
+
+
+def _solver(dims, pm, phases, precision, **kw):
+    from paper_2207_10657_gb300 import RVESolver, build
+    build.build()
+    return RVESolver(dims, pm, phases, precision=precision, **kw)
+
+
+def _oracle_rve(pm, phases, free=None):
+    return oracle.RVE(pm, [oracle.Phase(*p) if p[2] else oracle.Phase(p[0], p[1]) for p in phases], free_mask=free)
+
+
+def _to_dev(a, precision):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32 if precision == 32 else np.float64)).cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+GRIDS = [(32, 24), (30, 40), (2, 2), (1024, 8), (8, 12, 10), (16, 16, 16), (24, 20, 18), (2, 2, 2),
+         (6, 4, 1024)]
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("dims", GRIDS)
+def test_project_matches_oracle(dims, precision):
+    nd = len(dims)
+    nc = 3 if nd == 2 else 6
+    pm = np.zeros(tuple(reversed(dims)), np.uint8)
+    s = _solver(dims, pm, [MATRIX], precision)
+    for free in (None, [1] + [0] * (nc - 2) + [1]):
+        if free is not None:
+            s.set_free_mask(free)
+        v = random_field(nc, dims, seed=11)
+        out = s.project(_to_dev(v, precision)).cpu().numpy()
+        ref = oracle.project(v, None if free is None else np.array(free, bool))
+        assert _rel(out, ref) < TOL[precision], (dims, free)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("dims", [(32, 24), (64, 30), (8, 12, 10), (16, 16, 16), (24, 20, 18), (40, 36, 12)])
+def test_hessp_matches_oracle(dims, precision):
+    nd = len(dims)
+    nc = 3 if nd == 2 else 6
+    if nd == 2:
+        pm = circular_inclusion(dims, 0.3)
+    else:
+        pm = random_spheres(dims, count=5, rmin=1.5, rmax=3.5, seed=4)
+    D = damage_snapshot(pm, dmax=0.9, seed=1)
+    s = _solver(dims, pm, [MATRIX, STIFF], precision)
+    s.set_damage(torch.from_numpy(D).cuda())
+    v = random_field(nc, dims, seed=2)
+    out = s.hessp(_to_dev(v, precision)).cpu().numpy()
+    ref = _oracle_rve(pm, [MATRIX, STIFF]).hessp(D.astype(np.float64), v)
+    assert _rel(out, ref) < 5 * TOL[precision]
+    # in-place (aliased) call
+    x = _to_dev(v, precision)
+    s.hessp(x, out=x)
+    assert _rel(x.cpu().numpy(), ref) < 5 * TOL[precision]
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("dims", [(32, 32), (12, 16, 10)])
+def test_state_stress_damage_and_energy(dims, precision):
+    """Constitutive update (Appendix A) and the first-order incremental energy
+    (Eq. (18)) against the oracle."""
+    nd = len(dims)
+    nc = 3 if nd == 2 else 6
+    pm = circular_inclusion(dims, 0.3) if nd == 2 else random_spheres(dims, count=3, rmin=1.5, rmax=3.0, seed=5)
+    rng = np.random.default_rng(3)
+    eps = rng.standard_normal((nc,) + pm.shape) * 4e-4
+    kh = rng.uniform(0, 6e-4, pm.shape).astype(np.float32)
+    s = _solver(dims, pm, [MATRIX, STIFF], precision)
+    s.set_state(_to_dev(eps, precision), torch.from_numpy(kh).cuda())
+    st = s.get_state()
+    orv = _oracle_rve(pm, [MATRIX, STIFF])
+    sig, D, kap = orv.stress(eps, kh.astype(np.float64))
+    # damage: identical except within 1e-3 of the threshold kappa0
+    near = np.abs(kap - 1e-4) <= 1e-3 * 1e-4
+    dg = st["damage"].cpu().numpy()
+    assert np.max(np.abs(dg - D)[~near]) < (1e-5 if precision == 32 else 1e-12)
+    assert _rel(st["sigma"].cpu().numpy(), sig) < 20 * TOL[precision]
+    p = rng.standard_normal((nc,) + pm.shape) * 2e-4
+    dW, dm, grad = s.energy_grad(_to_dev(p, precision))
+    sig_t, _, _ = orv.stress(eps + p, kh.astype(np.float64))
+    dW_ref = 0.5 * (np.sum(sig * p) + np.sum(sig_t * p))
+    dm_ref = np.sum(sig * p) + 0.5 * np.sum(p * orv.tangent(D, p))
+    tol = 1e-5 if precision == 32 else 1e-11
+    assert abs(dW - dW_ref) <= tol * abs(dW_ref)
+    assert abs(dm - dm_ref) <= tol * abs(dm_ref)
+    assert _rel(grad.cpu().numpy(), orv.gradient(sig_t)) < 20 * TOL[precision]
+    s.close()
+
+
+def _oracle_curve(pm, phases, incs, free, prm):
+    from oracle.solver import load_path
+    orv = _oracle_rve(pm, phases, free)
+    return load_path(orv, incs, prm)
+
+
+def test_load_path_2d_plane_strain_fp64():
+    """32x32 plane strain, centred inclusion (vol. frac. 0.3), eps_xx ramped
+    0 -> 2e-3 in 20 increments, other components free: the homogenised
+    stress-strain curve matches the oracle along the softening branch."""
+    from oracle.solver import TRParams
+    dims = (32, 32)
+    pm = circular_inclusion(dims, 0.3)
+    phases = [MATRIX, (10.0, 0.3, False, 0.0, 0.0)]
+    free = [0, 1, 1]
+    incs = [np.array([1e-4, 0, 0])] * 20
+    R0 = 10 * np.sqrt(32 * 32) * 1e-4
+    # the secant Hessian makes Newton converge linearly once damage grows:
+    # generous iteration caps on both sides
+    prm = TRParams(eta_eq=1e-8, eta_cg=1e-10, R0=R0, Rmax=R0, max_nr=400, max_cg=500)
+    ref = _oracle_curve(pm, phases, incs, np.array(free, bool), prm)
+    s = _solver(dims, pm, phases, 64, eta_eq=1e-8, eta_cg=1e-10, R0=R0, Rmax=R0, max_nr=400, max_cg=500)
+    sig_gpu = []
+    for n, dE in enumerate(incs):
+        rep = s.solve_step(dE, free_mask=free)
+        assert rep["converged"], (n, rep)
+        sig_gpu.append(rep["mean_stress"][:3])
+    sig_gpu = np.array(sig_gpu)
+    sref = ref["mean_stress"]
+    scale = np.max(np.abs(sref[:, 0]))
+    err = np.max(np.abs(sig_gpu[:, 0] - sref[:, 0])) / scale
+    assert err < 1e-4, err
+    st = s.get_state()
+    kap_gpu = st["kappa"].cpu().numpy()
+    dmg_ref = ref["kappa"] > 1e-4
+    near = np.abs(ref["kappa"] - 1e-4) <= 1e-3 * 1e-4
+    assert np.array_equal((kap_gpu > 1e-4)[~near], dmg_ref[~near])
+    s.close()
+
+
+def test_load_path_3d_fp32_uniaxial():
+    """16^3 spheres in a damaging matrix, uniaxial eps_zz with the other
+    components free, FP32 fields with FP64 reductions, relative residual
+    1e-6: the elastic increment and the onset of damage give homogenised
+    stresses within 1e-5 / 1e-4 of the oracle's."""
+    from oracle.solver import TRParams
+    dims = (16, 16, 16)
+    pm = random_spheres(dims, count=6, rmin=2.0, rmax=3.5, seed=7)
+    phases = [MATRIX, STIFF]
+    free = [1, 1, 0, 1, 1, 1]
+    incs = [np.array([0, 0, 4e-5, 0, 0, 0])] * 2
+    R0 = 10 * np.sqrt(16 ** 3) * 4e-5
+    prm = TRParams(eta_eq=1e-6, eta_cg=1e-2, R0=R0, Rmax=R0, max_nr=300)
+    ref = _oracle_curve(pm, phases, incs, np.array(free, bool), prm)
+    s = _solver(dims, pm, phases, 32, eta_eq=1e-6, eta_cg=1e-2, R0=R0, Rmax=R0, max_nr=300)
+    out = []
+    for dE in incs:
+        rep = s.solve_step(dE, free_mask=free)
+        assert rep["converged"]
+        out.append(rep["mean_stress"])
+    out = np.array(out)
+    sref = ref["mean_stress"]
+    assert abs(out[0, 2] - sref[0, 2]) <= 1e-5 * abs(sref[0, 2])
+    assert abs(out[1, 2] - sref[1, 2]) <= 1e-4 * abs(sref[1, 2])
+    s.close()
+
+
+def test_laminate_closed_form_gpu():
+    """Bilayer laminate normal to z (interfaces on voxel faces): the GPU
+    solve reproduces the exact per-layer strains."""
+    dims = (8, 8, 16)
+    pm = laminate(dims, axis=2)
+    phases = [(1.0, 0.0, False, 0.0, 0.0), (10.0, 0.0, False, 0.0, 0.0)]
+    s = _solver(dims, pm, phases, 64, eta_eq=1e-12, eta_cg=1e-12, R0=1e3, Rmax=1e3)
+    rep = s.solve_step([0, 0, 1e-3, 0, 0, 0])
+    assert rep["converged"]
+    eps = s.get_state()["eps"].cpu().numpy()
+    # nu = 0: Reuss along z -> e_a E_a = e_b E_b, mean 1e-3
+    ea = 2e-3 * 10.0 / 11.0
+    eb = 2e-3 - ea
+    np.testing.assert_allclose(eps[2, :8], ea, rtol=1e-10)
+    np.testing.assert_allclose(eps[2, 8:], eb, rtol=1e-10)
+    assert abs(rep["mean_stress"][2] - 1e-3 / (0.5 / 1.0 + 0.5 / 10.0)) < 1e-12
+    s.close()
+
+
+def _plane_wave(A, k, dims):
+    """Re(A e^{i k.x}) in float32, phase index reduced exactly mod N."""
+    nx, ny, nz = dims
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij", sparse=True)
+    n = nx
+    assert nx == ny == nz
+    idx = (k[0] * x + k[1] * y + k[2] * z) % n
+    c = np.cos(2 * np.pi * np.arange(n) / n)[idx]
+    s = np.sin(2 * np.pi * np.arange(n) / n)[idx]
+    return np.stack([(a.real * c - a.imag * s).astype(np.float32) for a in A])
+
+
+def test_full_size_256_plane_wave_and_symmetry():
+    """At the benchmark size (256^3, FP32, the launch configuration the bench
+    times): single Fourier modes are projected exactly as the oracle's
+    per-frequency operator predicts, and the Hessian-vector product is
+    symmetric, positive and compatible (G H v = H v) on a heterogeneous
+    damage snapshot."""
+    dims = (256, 256, 256)
+    pm = random_spheres(dims, count=144, rmin=4.0, rmax=10.0, seed=0)
+    D = damage_snapshot(pm, dmax=0.9, seed=1)
+    s = _solver(dims, pm, [MATRIX, STIFF], 32)
+    rng = np.random.default_rng(0)
+    for k in [(3, 250, 129), (128, 0, 17), (0, 128, 128), (77, 1, 255)]:
+        A = rng.standard_normal(6) + 1j * rng.standard_normal(6)
+        field = _plane_wave(A, k, dims)
+        out = s.project(_to_dev(field, 32)).cpu().numpy()
+        GA = oracle.project_one(A, oracle.gradient_symbol_at(k, dims))
+        # the Nyquist-x mode is its own conjugate: only Re(GA e^{ikx}) survives
+        ref = _plane_wave(GA, k, dims)
+        scale = max(np.linalg.norm(ref), 1e-3 * np.linalg.norm(field))
+        assert np.linalg.norm(out - ref) / scale < 5e-6, k
+        del field, out, ref
+    s.set_damage(torch.from_numpy(D).cuda())
+    u = s.project(_to_dev(random_field(6, dims, seed=5, dtype=np.float32), 32))
+    w = s.project(_to_dev(random_field(6, dims, seed=6, dtype=np.float32), 32))
+    Hu, Hw = s.hessp(u), s.hessp(w)
+    a = torch.sum(u.double() * Hw.double()).item()
+    b = torch.sum(Hu.double() * w.double()).item()
+    assert abs(a - b) <= 1e-5 * abs(a)
+    GHu = s.project(Hu)
+    assert (torch.linalg.vector_norm((GHu - Hu).double()) / torch.linalg.vector_norm(Hu.double())).item() < 1e-5
+    assert torch.sum(u.double() * Hu.double()).item() > 0
+    s.close()

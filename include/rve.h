@@ -108,19 +108,21 @@ rve_status rve_create(const int dims[3], int ndim, const uint8_t* phase_ids_dev,
                       const rve_phase* phases_host, int nphase,
                       const rve_solver_opts* opts_host, void* stream, rve_t* out);
 
-/* Set the state: total strain (ncomp x Nvox, real type of the context) and
- * committed history kappa_n (Nvox floats, NULL = 0).  Recomputes sigma and
+/* Set the state: total strain (ncomp x Nvox) and committed history kappa_n
+ * (Nvox, NULL = 0), both of the context's real type.  Recomputes sigma and
  * D at the state (Appendix A, with kappa = max(kappa_n, kappa(eps))). */
-rve_status rve_set_state(rve_t, const void* strain_dev, const float* kappa_hist_dev);
+rve_status rve_set_state(rve_t, const void* strain_dev, const void* kappa_hist_dev);
 
-/* Copy out the state; any pointer may be NULL.  stress_dev receives sigma
- * at the state, damage_dev the damage D (Nvox floats). */
-rve_status rve_get_state(rve_t, void* strain_dev, float* kappa_dev, void* stress_dev,
-                         float* damage_dev);
+/* Copy out the state; any pointer may be NULL.  strain_dev / stress_dev:
+ * ncomp x Nvox; kappa_dev (committed history) / damage_dev (damage D at the
+ * state): Nvox.  All of the context's real type. */
+rve_status rve_get_state(rve_t, void* strain_dev, void* kappa_dev, void* stress_dev,
+                         void* damage_dev);
 
-/* Replace the frozen damage field used by rve_hessp (Nvox floats in [0,1]).
- * For benchmarking the Hessian-vector product on a damage snapshot. */
-rve_status rve_set_damage(rve_t, const float* damage_dev);
+/* Replace the frozen damage field used by rve_hessp (Nvox values in [0,1],
+ * context's real type).  For the Hessian-vector product on a damage
+ * snapshot (benchmarks, tests). */
+rve_status rve_set_damage(rve_t, const void* damage_dev);
 
 /* Stress-controlled mean components (zero mean stress): free_mask[c] != 0
  * for Mandel component c.  Sets Ghat(0) = P_free (mixed control, Sec. 3.3). */

@@ -207,7 +207,7 @@ __device__ void fft_lines(C* buf, const AxisPlan& p, int nlines, const LineMap l
 template <typename R> struct MatTable {
   int nphase;
   R lam[kMaxPhases], mu[kMaxPhases];
-  float kappa0[kMaxPhases], kappaf[kMaxPhases];
+  R kappa0[kMaxPhases], kappaf[kMaxPhases];
   int damaging[kMaxPhases];
 };
 

@@ -1,0 +1,394 @@
+// FP32 spectral passes specialised at compile time for the common axis
+// lengths (powers of two from 32 to 512 and 3 * 2^k up to 384).  Same data
+// layout and the same arithmetic as the generic passes in hv_passes.cu;
+// only the FFT engine (fft_fast.cuh) and the global I/O (float4 rows)
+// differ.
+#include "fft_fast.cuh"
+#include "hv_passes.cuh"
+#include "hv_fast.cuh"
+#include "project.cuh"
+
+namespace rve {
+
+constexpr int kFT = 256;       // threads of the x / y passes
+constexpr int kFBudget = 4096; // complex elements per x / y block
+
+template <int N, int NC> constexpr int xq() {
+  // voxel rows per x block: NC*Q/2 lines of N, prefer an odd line count
+  constexpr int nlmax = kFBudget / N;
+  constexpr int q0 = (2 * nlmax) / NC;
+  constexpr int q1 = (NC & 1) ? (q0 & ~1) : q0;
+  constexpr int q2 = (q1 < ((NC & 1) ? 2 : 1)) ? ((NC & 1) ? 2 : 1) : q1;
+  constexpr int nl = NC * q2 / 2;
+  return ((nl & 1) == 0 && q2 > ((NC & 1) ? 2 : 1)) ? q2 - ((NC & 1) ? 2 : 1) : q2;
+}
+template <int N> constexpr int ytx() { return (kFBudget / N) < 16 ? (kFBudget / N) : 16; }
+template <int N> constexpr int ztx() { return N <= 256 ? (N <= 64 ? 16 : 8) : 4; }
+template <int N> constexpr int zthreads() { return N >= 256 ? 512 : 256; }
+template <int N> constexpr int p2tx() { return (kFBudget / (3 * N)) < 16 ? (kFBudget / (3 * N)) : 16; }
+
+// ------------------------------------------------------------ x forward
+template <int N, int NC, int MODE>
+__global__ void __launch_bounds__(kFT)
+    kf_xfwd(const float* __restrict__ in, const uint8_t* __restrict__ phase, const float* __restrict__ dmg,
+            const MatTable<float> mt, float2* __restrict__ spec, const long long nrows, const long long nvox,
+            const float2* __restrict__ tw) {
+  constexpr int Q = xq<N, NC>();
+  constexpr int NL = NC * Q / 2;
+  constexpr int ND = NC == 6 ? 3 : 2;
+  constexpr int N4 = N / 4;
+  __shared__ __align__(16) float2 buf[NL * N];
+  const long long row0 = (long long)blockIdx.x * Q;
+  for (int idx = threadIdx.x; idx < Q * N4; idx += kFT) {
+    const int q = idx / N4, x4 = idx - (idx / N4) * N4;
+    const long long row = row0 + q;
+    float4 v[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) v[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (row < nrows) {
+      const long long vox = row * N + 4 * x4;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) v[c] = __ldg(reinterpret_cast<const float4*>(in + c * nvox + vox));
+      if (MODE == 1) {
+        const float4 d4 = __ldg(reinterpret_cast<const float4*>(dmg + vox));
+        const uchar4 p4 = __ldg(reinterpret_cast<const uchar4*>(phase + vox));
+        const float dd[4] = {d4.x, d4.y, d4.z, d4.w};
+        const int pp[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float keep = 1.f - dd[e];
+          const float lam = mt.lam[pp[e]] * keep, tmu = 2.f * mt.mu[pp[e]] * keep;
+          float* f[NC];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) f[c] = reinterpret_cast<float*>(&v[c]) + e;
+          float tr = 0.f;
+#pragma unroll
+          for (int i = 0; i < ND; ++i) tr += *f[i];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) *f[c] = tmu * *f[c] + (c < ND ? lam * tr : 0.f);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int rho = q * NC + c;
+      const int p = rho >> 1, h = rho & 1;
+      const float* ve = reinterpret_cast<const float*>(&v[c]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) reinterpret_cast<float*>(&buf[(4 * x4 + e) * NL + p])[h] = ve[e];
+    }
+  }
+  __syncthreads();
+  fft_ct<N, NL, kFT, false>(buf, tw);
+  constexpr int NXH = N / 2 + 1;
+  for (int idx = threadIdx.x; idx < NL * NXH; idx += kFT) {
+    const int p = idx / NXH, k = idx - (idx / NXH) * NXH;
+    const float2 zk = buf[k * NL + p];
+    const float2 zm = buf[((N - k) % N) * NL + p];
+    const float2 xa = make_float2((zk.x + zm.x) * 0.5f, (zk.y - zm.y) * 0.5f);
+    const float2 xb = make_float2((zk.y + zm.y) * 0.5f, (zm.x - zk.x) * 0.5f);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int rho = 2 * p + h;
+      const int q = rho / NC, c = rho - (rho / NC) * NC;
+      const long long row = row0 + q;
+      if (row < nrows) spec[(c * nrows + row) * NXH + k] = h ? xb : xa;
+    }
+  }
+}
+
+// ------------------------------------------------------------ x inverse
+template <int N, int NC, bool DOT>
+__global__ void __launch_bounds__(kFT)
+    kf_xinv(const float2* __restrict__ spec, float* __restrict__ out, const float* __restrict__ dotw,
+            double* __restrict__ partials, const long long nrows, const long long nvox,
+            const float2* __restrict__ tw, const float scale, const bool self_dot) {
+  constexpr int Q = xq<N, NC>();
+  constexpr int NL = NC * Q / 2;
+  constexpr int N4 = N / 4;
+  constexpr int NXH = N / 2 + 1;
+  constexpr int HALF = N / 2;
+  __shared__ __align__(16) float2 buf[NL * N];
+  __shared__ double red[32];
+  const long long row0 = (long long)blockIdx.x * Q;
+  for (int idx = threadIdx.x; idx < NL * N; idx += kFT) {
+    const int p = idx / N, k = idx - (idx / N) * N;
+    float2 xh[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int rho = 2 * p + h;
+      const int q = rho / NC, c = rho - (rho / NC) * NC;
+      const long long row = row0 + q;
+      float2 x = make_float2(0.f, 0.f);
+      if (row < nrows) {
+        const int kk = k <= HALF ? k : N - k;
+        x = spec[(c * nrows + row) * NXH + kk];
+        if (kk == 0 || kk == HALF) x.y = 0.f;
+        if (k > HALF) x.y = -x.y;
+      }
+      xh[h] = x;
+    }
+    buf[k * NL + p] = make_float2(xh[0].x - xh[1].y, xh[0].y + xh[1].x);
+  }
+  __syncthreads();
+  fft_ct<N, NL, kFT, true>(buf, tw);
+  KSum<float> acc;
+  for (int idx = threadIdx.x; idx < Q * NC * N4; idx += kFT) {
+    const int rho = idx / N4, x4 = idx - (idx / N4) * N4;
+    const int q = rho / NC, c = rho - (rho / NC) * NC;
+    const long long row = row0 + q;
+    if (row < nrows) {
+      const int p = rho >> 1, h = rho & 1;
+      float4 o;
+      float* oe = reinterpret_cast<float*>(&o);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) oe[e] = reinterpret_cast<const float*>(&buf[(4 * x4 + e) * NL + p])[h] * scale;
+      const long long off = c * nvox + row * N + 4 * x4;
+      *reinterpret_cast<float4*>(out + off) = o;
+      if (DOT) {
+        if (self_dot) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc.add(oe[e] * oe[e]);
+        } else {
+          const float4 w = __ldg(reinterpret_cast<const float4*>(dotw + off));
+          acc.add(o.x * w.x);
+          acc.add(o.y * w.y);
+          acc.add(o.z * w.z);
+          acc.add(o.w * w.w);
+        }
+      }
+    }
+  }
+  if (DOT) {
+    double v[1] = {acc.value()};
+    block_sum<1>(v, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+  }
+}
+
+// ------------------------------------------------------------ y columns
+template <int N, bool INV>
+__global__ void __launch_bounds__(kFT)
+    kf_ycols(float2* __restrict__ spec, const int nz, const int nxh, const float2* __restrict__ tw) {
+  constexpr int TX = ytx<N>();
+  __shared__ __align__(16) float2 buf[TX * N];
+  const int kx0 = blockIdx.x * TX;
+  const int tv = min(TX, nxh - kx0);
+  const long long plane = ((long long)blockIdx.z * nz + blockIdx.y) * N;
+  for (int idx = threadIdx.x; idx < N * TX; idx += kFT) {
+    const int y = idx / TX, t = idx - (idx / TX) * TX;
+    buf[idx] = t < tv ? spec[(plane + y) * nxh + kx0 + t] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_ct<N, TX, kFT, INV>(buf, tw);
+  for (int idx = threadIdx.x; idx < N * TX; idx += kFT) {
+    const int y = idx / TX, t = idx - (idx / TX) * TX;
+    if (t < tv) spec[(plane + y) * nxh + kx0 + t] = buf[idx];
+  }
+}
+
+// ------------------------------------------------- z + projection (3D)
+template <int N>
+__global__ void __launch_bounds__(zthreads<N>())
+    kf_zproj(float2* __restrict__ spec, const int ny, const int nxh, const float2* __restrict__ tw,
+             const float2* __restrict__ gdx, const float2* __restrict__ gax, const float2* __restrict__ gdy,
+             const float2* __restrict__ gay, const float2* __restrict__ gdz, const float2* __restrict__ gaz,
+             const unsigned free_mask) {
+  constexpr int TX = ztx<N>();
+  constexpr int NL = 6 * TX;
+  constexpr int NT = zthreads<N>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* buf = reinterpret_cast<float2*>(smem_raw);
+  const int kx0 = blockIdx.x * TX, ky = blockIdx.y;
+  const int tv = min(TX, nxh - kx0);
+  for (int idx = threadIdx.x; idx < N * NL; idx += NT) {
+    const int z = idx / NL, rem = idx - (idx / NL) * NL;
+    const int c = rem / TX, t = rem - (rem / TX) * TX;
+    buf[idx] = t < tv ? spec[(((long long)c * N + z) * ny + ky) * nxh + kx0 + t] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_ct<N, NL, NT, false>(buf, tw);
+  const float2 ay = gay[ky], dy = gdy[ky];
+  for (int pt = threadIdx.x; pt < N * TX; pt += NT) {
+    const int z = pt / TX, t = pt - (pt / TX) * TX;
+    const int kx = kx0 + t;
+    if (t >= tv) continue;
+    float2 m[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) m[c] = buf[z * NL + c * TX + t];
+    const float2 ax = gax[kx], dx = gdx[kx], az = gaz[z], dz = gdz[z];
+    project3<float>(m, cmul(cmul(dx, ay), az), cmul(cmul(ax, dy), az), cmul(cmul(ax, ay), dz),
+                    kx == 0 && ky == 0 && z == 0, free_mask);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) buf[z * NL + c * TX + t] = m[c];
+  }
+  __syncthreads();
+  fft_ct<N, NL, NT, true>(buf, tw);
+  for (int idx = threadIdx.x; idx < N * NL; idx += NT) {
+    const int z = idx / NL, rem = idx - (idx / NL) * NL;
+    const int c = rem / TX, t = rem - (rem / TX) * TX;
+    if (t < tv) spec[(((long long)c * N + z) * ny + ky) * nxh + kx0 + t] = buf[idx];
+  }
+}
+
+// ------------------------------------------------- y + projection (2D)
+template <int N>
+__global__ void __launch_bounds__(kFT)
+    kf_yproj2d(float2* __restrict__ spec, const int nxh, const float2* __restrict__ tw,
+               const float2* __restrict__ gdx, const float2* __restrict__ gax, const float2* __restrict__ gdy,
+               const float2* __restrict__ gay, const unsigned free_mask) {
+  constexpr int TX = p2tx<N>();
+  constexpr int NL = 3 * TX;
+  __shared__ __align__(16) float2 buf[N * NL];
+  const int kx0 = blockIdx.x * TX;
+  const int tv = min(TX, nxh - kx0);
+  for (int idx = threadIdx.x; idx < N * NL; idx += kFT) {
+    const int y = idx / NL, rem = idx - (idx / NL) * NL;
+    const int c = rem / TX, t = rem - (rem / TX) * TX;
+    buf[idx] = t < tv ? spec[((long long)c * N + y) * nxh + kx0 + t] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_ct<N, NL, kFT, false>(buf, tw);
+  for (int pt = threadIdx.x; pt < N * TX; pt += kFT) {
+    const int y = pt / TX, t = pt - (pt / TX) * TX;
+    const int kx = kx0 + t;
+    if (t >= tv) continue;
+    float2 m[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m[c] = buf[y * NL + c * TX + t];
+    project2<float>(m, cmul(gdx[kx], gay[y]), cmul(gax[kx], gdy[y]), kx == 0 && y == 0, free_mask);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) buf[y * NL + c * TX + t] = m[c];
+  }
+  __syncthreads();
+  fft_ct<N, NL, kFT, true>(buf, tw);
+  for (int idx = threadIdx.x; idx < N * NL; idx += kFT) {
+    const int y = idx / NL, rem = idx - (idx / NL) * NL;
+    const int c = rem / TX, t = rem - (rem / TX) * TX;
+    if (t < tv) spec[((long long)c * N + y) * nxh + kx0 + t] = buf[idx];
+  }
+}
+
+// ================================================================ dispatch
+#define RVE_FAST_SIZES(X) X(32) X(64) X(128) X(256) X(512) X(96) X(192) X(384)
+
+bool fast_size(int n) {
+#define RVE_CASE(n_) if (n == n_) return true;
+  RVE_FAST_SIZES(RVE_CASE)
+#undef RVE_CASE
+  return false;
+}
+
+template <int N>
+static cudaError_t xfwd_n(const GridDesc& g, const float* in, const uint8_t* phase, const float* dmg,
+                          const MatTable<float>& mt, float2* spec, const float2* tw, bool tangent, cudaStream_t st) {
+  if (g.ncomp == 6) {
+    constexpr int Q = xq<N, 6>();
+    const int blocks = (int)((g.nrows + Q - 1) / Q);
+    if (tangent) kf_xfwd<N, 6, 1><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw);
+    else kf_xfwd<N, 6, 0><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw);
+  } else {
+    constexpr int Q = xq<N, 3>();
+    const int blocks = (int)((g.nrows + Q - 1) / Q);
+    if (tangent) kf_xfwd<N, 3, 1><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw);
+    else kf_xfwd<N, 3, 0><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw);
+  }
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t xinv_n(const GridDesc& g, const float2* spec, float* out, const float* dotw, double* partials,
+                          const float2* tw, bool dot, bool self, int* nblocks, cudaStream_t st) {
+  const float scale = (float)(1.0 / (double)g.nvox);
+  if (g.ncomp == 6) {
+    constexpr int Q = xq<N, 6>();
+    const int blocks = (int)((g.nrows + Q - 1) / Q);
+    *nblocks = blocks;
+    if (dot) kf_xinv<N, 6, true><<<blocks, kFT, 0, st>>>(spec, out, dotw, partials, g.nrows, g.nvox, tw, scale, self);
+    else kf_xinv<N, 6, false><<<blocks, kFT, 0, st>>>(spec, out, dotw, partials, g.nrows, g.nvox, tw, scale, self);
+  } else {
+    constexpr int Q = xq<N, 3>();
+    const int blocks = (int)((g.nrows + Q - 1) / Q);
+    *nblocks = blocks;
+    if (dot) kf_xinv<N, 3, true><<<blocks, kFT, 0, st>>>(spec, out, dotw, partials, g.nrows, g.nvox, tw, scale, self);
+    else kf_xinv<N, 3, false><<<blocks, kFT, 0, st>>>(spec, out, dotw, partials, g.nrows, g.nvox, tw, scale, self);
+  }
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t ycols_n(const GridDesc& g, float2* spec, const float2* tw, bool inv, cudaStream_t st) {
+  constexpr int TX = ytx<N>();
+  const dim3 grid((g.nxh + TX - 1) / TX, g.nz, g.ncomp);
+  if (inv) kf_ycols<N, true><<<grid, kFT, 0, st>>>(spec, g.nz, g.nxh, tw);
+  else kf_ycols<N, false><<<grid, kFT, 0, st>>>(spec, g.nz, g.nxh, tw);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t zproj_n(const GridDesc& g, float2* spec, const SpecWork<float>& w, cudaStream_t st) {
+  constexpr int TX = ztx<N>();
+  const size_t smem = (size_t)N * 6 * TX * sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(kf_zproj<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  const dim3 grid((g.nxh + TX - 1) / TX, g.ny);
+  kf_zproj<N><<<grid, zthreads<N>(), smem, st>>>(spec, g.ny, g.nxh, w.tw[2], w.gdiff[0], w.gavg[0], w.gdiff[1],
+                                                  w.gavg[1], w.gdiff[2], w.gavg[2], w.free_mask);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t yproj2d_n(const GridDesc& g, float2* spec, const SpecWork<float>& w, cudaStream_t st) {
+  constexpr int TX = p2tx<N>();
+  const dim3 grid((g.nxh + TX - 1) / TX);
+  kf_yproj2d<N><<<grid, kFT, 0, st>>>(spec, g.nxh, w.tw[1], w.gdiff[0], w.gavg[0], w.gdiff[1], w.gavg[1],
+                                       w.free_mask);
+  return cudaGetLastError();
+}
+
+cudaError_t fast_xfwd(const GridDesc& g, const float* in, const uint8_t* phase, const float* dmg,
+                      const MatTable<float>& mt, float2* spec, const float2* tw, bool tangent, cudaStream_t st) {
+#define RVE_CASE(n_) \
+  if (g.nx == n_) return xfwd_n<n_>(g, in, phase, dmg, mt, spec, tw, tangent, st);
+  RVE_FAST_SIZES(RVE_CASE)
+#undef RVE_CASE
+  return cudaErrorNotSupported;
+}
+
+cudaError_t fast_xinv(const GridDesc& g, const float2* spec, float* out, const float* dotw, double* partials,
+                      const float2* tw, bool dot, bool self, int* nblocks, cudaStream_t st) {
+#define RVE_CASE(n_) \
+  if (g.nx == n_) return xinv_n<n_>(g, spec, out, dotw, partials, tw, dot, self, nblocks, st);
+  RVE_FAST_SIZES(RVE_CASE)
+#undef RVE_CASE
+  return cudaErrorNotSupported;
+}
+
+cudaError_t fast_ycols(const GridDesc& g, float2* spec, const float2* tw, bool inv, cudaStream_t st) {
+#define RVE_CASE(n_) \
+  if (g.ny == n_) return ycols_n<n_>(g, spec, tw, inv, st);
+  RVE_FAST_SIZES(RVE_CASE)
+#undef RVE_CASE
+  return cudaErrorNotSupported;
+}
+
+cudaError_t fast_zproj(const GridDesc& g, float2* spec, const SpecWork<float>& w, cudaStream_t st) {
+#define RVE_CASE(n_) \
+  if (g.nz == n_) return zproj_n<n_>(g, spec, w, st);
+  RVE_FAST_SIZES(RVE_CASE)
+#undef RVE_CASE
+  return cudaErrorNotSupported;
+}
+
+cudaError_t fast_yproj2d(const GridDesc& g, float2* spec, const SpecWork<float>& w, cudaStream_t st) {
+#define RVE_CASE(n_) \
+  if (g.ny == n_) return yproj2d_n<n_>(g, spec, w, st);
+  RVE_FAST_SIZES(RVE_CASE)
+#undef RVE_CASE
+  return cudaErrorNotSupported;
+}
+
+}  // namespace rve

@@ -1,0 +1,19 @@
+// Dispatch into the compile-time-specialised FP32 passes (hv_fast.cu).
+// Each returns cudaErrorNotSupported when the axis length has no
+// specialisation; the caller then uses the generic pass.
+#pragma once
+
+#include "hv_passes.cuh"
+
+namespace rve {
+
+bool fast_size(int n);
+cudaError_t fast_xfwd(const GridDesc& g, const float* in, const uint8_t* phase, const float* dmg,
+                      const MatTable<float>& mt, float2* spec, const float2* tw, bool tangent, cudaStream_t st);
+cudaError_t fast_xinv(const GridDesc& g, const float2* spec, float* out, const float* dotw, double* partials,
+                      const float2* tw, bool dot, bool self, int* nblocks, cudaStream_t st);
+cudaError_t fast_ycols(const GridDesc& g, float2* spec, const float2* tw, bool inv, cudaStream_t st);
+cudaError_t fast_zproj(const GridDesc& g, float2* spec, const SpecWork<float>& w, cudaStream_t st);
+cudaError_t fast_yproj2d(const GridDesc& g, float2* spec, const SpecWork<float>& w, cudaStream_t st);
+
+}  // namespace rve

@@ -10,7 +10,11 @@
 #include <cmath>
 #include <vector>
 
+#include <type_traits>
+
+#include "hv_fast.cuh"
 #include "hv_passes.cuh"
+#include "project.cuh"
 
 namespace rve {
 
@@ -18,75 +22,6 @@ constexpr int kXThreads = 256, kXEpt = 16;  // x passes
 constexpr int kYThreads = 256, kYEpt = 16;  // y columns, 2D y+projection
 constexpr int kZThreads = 512, kZEpt = 24;  // z + projection
 constexpr int kSmemCap = 100 * 1024;        // dynamic shared memory cap per block
-
-// ------------------------------------------------------------ projection
-// Ghat(k) : zeta for one frequency, Mandel components m (complex).
-// n = Dhat/|Dhat|, v = zeta n*, s = n*^T zeta n*,
-// Ghat:zeta = n (x) v + v (x) n - s n (x) n.  Ghat = 0 where Dhat = 0
-// (k != 0); Ghat(0) keeps the stress-controlled (free) components.
-template <typename R>
-__device__ __forceinline__ void project3(Cx<R> (&m)[6], Cx<R> d0, Cx<R> d1, Cx<R> d2, bool k0,
-                                         unsigned free_mask) {
-  using C = Cx<R>;
-  if (k0) {
-#pragma unroll
-    for (int c = 0; c < 6; ++c)
-      if (!((free_mask >> c) & 1u)) m[c] = C{0, 0};
-    return;
-  }
-  const R n2 = d0.x * d0.x + d0.y * d0.y + d1.x * d1.x + d1.y * d1.y + d2.x * d2.x + d2.y * d2.y;
-  if (n2 == (R)0) {
-#pragma unroll
-    for (int c = 0; c < 6; ++c) m[c] = C{0, 0};
-    return;
-  }
-  const R inv = (R)1 / sqrt(n2);
-  const C n[3] = {cscale(d0, inv), cscale(d1, inv), cscale(d2, inv)};
-  const R is2 = (R)0.70710678118654752440, s2 = (R)1.41421356237309504880;
-  const C t00 = m[0], t11 = m[1], t22 = m[2];
-  const C t12 = cscale(m[3], is2), t02 = cscale(m[4], is2), t01 = cscale(m[5], is2);
-  // v_i = sum_j T_ij conj(n_j)
-  const C v0 = cadd(cadd(cmulc(t00, n[0]), cmulc(t01, n[1])), cmulc(t02, n[2]));
-  const C v1 = cadd(cadd(cmulc(t01, n[0]), cmulc(t11, n[1])), cmulc(t12, n[2]));
-  const C v2 = cadd(cadd(cmulc(t02, n[0]), cmulc(t12, n[1])), cmulc(t22, n[2]));
-  // s = sum_i conj(n_i) v_i
-  const C s = cadd(cadd(cmulc(v0, n[0]), cmulc(v1, n[1])), cmulc(v2, n[2]));
-  auto o = [&](C ni, C nj, C vi, C vj) { return csub(cadd(cmul(ni, vj), cmul(vi, nj)), cmul(s, cmul(ni, nj))); };
-  m[0] = o(n[0], n[0], v0, v0);
-  m[1] = o(n[1], n[1], v1, v1);
-  m[2] = o(n[2], n[2], v2, v2);
-  m[3] = cscale(o(n[1], n[2], v1, v2), s2);
-  m[4] = cscale(o(n[0], n[2], v0, v2), s2);
-  m[5] = cscale(o(n[0], n[1], v0, v1), s2);
-}
-
-template <typename R>
-__device__ __forceinline__ void project2(Cx<R> (&m)[3], Cx<R> d0, Cx<R> d1, bool k0, unsigned free_mask) {
-  using C = Cx<R>;
-  if (k0) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      if (!((free_mask >> c) & 1u)) m[c] = C{0, 0};
-    return;
-  }
-  const R n2 = d0.x * d0.x + d0.y * d0.y + d1.x * d1.x + d1.y * d1.y;
-  if (n2 == (R)0) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) m[c] = C{0, 0};
-    return;
-  }
-  const R inv = (R)1 / sqrt(n2);
-  const C n0 = cscale(d0, inv), n1 = cscale(d1, inv);
-  const R is2 = (R)0.70710678118654752440, s2 = (R)1.41421356237309504880;
-  const C t00 = m[0], t11 = m[1], t01 = cscale(m[2], is2);
-  const C v0 = cadd(cmulc(t00, n0), cmulc(t01, n1));
-  const C v1 = cadd(cmulc(t01, n0), cmulc(t11, n1));
-  const C s = cadd(cmulc(v0, n0), cmulc(v1, n1));
-  auto o = [&](C ni, C nj, C vi, C vj) { return csub(cadd(cmul(ni, vj), cmul(vi, nj)), cmul(s, cmul(ni, nj))); };
-  m[0] = o(n0, n0, v0, v0);
-  m[1] = o(n1, n1, v1, v1);
-  m[2] = cscale(o(n0, n1, v0, v1), s2);
-}
 
 // ------------------------------------------------------------ x forward
 // Q voxel rows per block, all ncomp components of each row.  With the
@@ -96,7 +31,7 @@ __device__ __forceinline__ void project2(Cx<R> (&m)[3], Cx<R> d0, Cx<R> d1, bool
 // Hermitian symmetry of real-input spectra.
 template <typename R, int MODE>
 __global__ void __launch_bounds__(kXThreads)
-    k_xfwd(const R* __restrict__ in, const uint8_t* __restrict__ phase, const float* __restrict__ dmg,
+    k_xfwd(const R* __restrict__ in, const uint8_t* __restrict__ phase, const R* __restrict__ dmg,
            const MatTable<R> mt, Cx<R>* __restrict__ spec, const GridDesc g, const int Q, const AxisPlan px,
            const Cx<R>* __restrict__ tw) {
   using C = Cx<R>;
@@ -114,7 +49,7 @@ __global__ void __launch_bounds__(kXThreads)
       for (int c = 0; c < nc; ++c) val[c] = in[c * g.nvox + vox];
       if (MODE == 1) {
         const int ph = phase[vox];
-        const R keep = (R)1 - (R)dmg[vox];
+        const R keep = (R)1 - dmg[vox];
         const R lam = mt.lam[ph] * keep, two_mu = (R)2 * mt.mu[ph] * keep;
         R tr = 0;
         for (int i = 0; i < nd; ++i) tr += val[i];
@@ -442,51 +377,93 @@ void spectral_free(SpecWork<R>& w) {
 
 template <typename R>
 cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>& mt, const R* in,
-                           const uint8_t* phase, const float* damage, XIn mode, R* out,
+                           const uint8_t* phase, const R* damage, XIn mode, R* out,
                            const R* dot_with, double* dot_out, cudaStream_t st, long long* nlaunch) {
   using C = Cx<R>;
+  constexpr bool F32 = std::is_same<R, float>::value;
   long long nl = 0;
+  cudaError_t e;
   const int xblocks = (int)((g.nrows + w.qx - 1) / w.qx);
   const size_t xsm = (size_t)((g.ncomp * w.qx) / 2) * g.nx * sizeof(C);
-  if (mode == XIn::Tangent)
-    k_xfwd<R, 1><<<xblocks, kXThreads, xsm, st>>>(in, phase, damage, mt, w.spec, g, w.qx, w.px, w.tw[0]);
-  else
-    k_xfwd<R, 0><<<xblocks, kXThreads, xsm, st>>>(in, phase, damage, mt, w.spec, g, w.qx, w.px, w.tw[0]);
+  // x forward (tangent fused)
+  e = cudaErrorNotSupported;
+  if constexpr (F32) {
+    if (fast_size(g.nx))
+      e = fast_xfwd(g, in, phase, damage, mt, w.spec, w.tw[0], mode == XIn::Tangent, st);
+  }
+  if (e == cudaErrorNotSupported) {
+    if (mode == XIn::Tangent)
+      k_xfwd<R, 1><<<xblocks, kXThreads, xsm, st>>>(in, phase, damage, mt, w.spec, g, w.qx, w.px, w.tw[0]);
+    else
+      k_xfwd<R, 0><<<xblocks, kXThreads, xsm, st>>>(in, phase, damage, mt, w.spec, g, w.qx, w.px, w.tw[0]);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return e;
   ++nl;
   if (g.ndim == 3) {
     const dim3 yg((g.nxh + w.ty - 1) / w.ty, g.nz, g.ncomp);
     const size_t ysm = (size_t)w.ty * g.ny * sizeof(C);
-    k_ycols<R, false><<<yg, kYThreads, ysm, st>>>(w.spec, g, w.ty, w.py, w.tw[1]);
     const dim3 zg((g.nxh + w.tz - 1) / w.tz, g.ny);
     const size_t zsm = (size_t)6 * w.tz * g.nz * sizeof(C);
-    k_zproj<R><<<zg, kZThreads, zsm, st>>>(w.spec, g, w.tz, w.pz, w.tw[2], w.gdiff[0], w.gavg[0], w.gdiff[1],
-                                           w.gavg[1], w.gdiff[2], w.gavg[2], w.free_mask);
-    k_ycols<R, true><<<yg, kYThreads, ysm, st>>>(w.spec, g, w.ty, w.py, w.tw[1]);
-    nl += 3;
+    for (int pass = 0; pass < 3; ++pass) {
+      e = cudaErrorNotSupported;
+      if constexpr (F32) {
+        if (pass != 1 && fast_size(g.ny)) e = fast_ycols(g, w.spec, w.tw[1], pass == 2, st);
+        if (pass == 1 && fast_size(g.nz)) e = fast_zproj(g, w.spec, w, st);
+      }
+      if (e == cudaErrorNotSupported) {
+        if (pass == 0) k_ycols<R, false><<<yg, kYThreads, ysm, st>>>(w.spec, g, w.ty, w.py, w.tw[1]);
+        else if (pass == 2) k_ycols<R, true><<<yg, kYThreads, ysm, st>>>(w.spec, g, w.ty, w.py, w.tw[1]);
+        else
+          k_zproj<R><<<zg, kZThreads, zsm, st>>>(w.spec, g, w.tz, w.pz, w.tw[2], w.gdiff[0], w.gavg[0],
+                                                 w.gdiff[1], w.gavg[1], w.gdiff[2], w.gavg[2], w.free_mask);
+        e = cudaGetLastError();
+      }
+      if (e != cudaSuccess) return e;
+      ++nl;
+    }
   } else {
-    const dim3 pg((g.nxh + w.tz - 1) / w.tz);
-    const size_t psm = (size_t)3 * w.tz * g.ny * sizeof(C);
-    k_yproj2d<R><<<pg, kYThreads, psm, st>>>(w.spec, g, w.tz, w.py, w.tw[1], w.gdiff[0], w.gavg[0], w.gdiff[1],
-                                             w.gavg[1], w.free_mask);
+    e = cudaErrorNotSupported;
+    if constexpr (F32) {
+      if (fast_size(g.ny)) e = fast_yproj2d(g, w.spec, w, st);
+    }
+    if (e == cudaErrorNotSupported) {
+      const dim3 pg((g.nxh + w.tz - 1) / w.tz);
+      const size_t psm = (size_t)3 * w.tz * g.ny * sizeof(C);
+      k_yproj2d<R><<<pg, kYThreads, psm, st>>>(w.spec, g, w.tz, w.py, w.tw[1], w.gdiff[0], w.gavg[0], w.gdiff[1],
+                                               w.gavg[1], w.free_mask);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
     ++nl;
   }
   const R scale = (R)(1.0 / (double)g.nvox);
-  if (dot_with) {
-    const bool self = (dot_with == out);
-    k_xinv<R, true><<<xblocks, kXThreads, xsm, st>>>(w.spec, out, self ? nullptr : dot_with, w.partials, g, w.qx,
-                                                     w.px, w.tw[0], scale, self);
-    ++nl;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = reduce_partials(w.partials, xblocks, 1, dot_out, st, &nl);
-    if (nlaunch) *nlaunch += nl;
-    return e;
+  const bool dot = dot_with != nullptr;
+  const bool self = dot && (dot_with == out);
+  int nblocks = xblocks;
+  e = cudaErrorNotSupported;
+  if constexpr (F32) {
+    if (fast_size(g.nx))
+      e = fast_xinv(g, w.spec, out, self ? nullptr : dot_with, w.partials, w.tw[0], dot, self, &nblocks, st);
   }
-  k_xinv<R, false><<<xblocks, kXThreads, xsm, st>>>(w.spec, out, nullptr, nullptr, g, w.qx, w.px, w.tw[0], scale,
-                                                    false);
+  if (e == cudaErrorNotSupported) {
+    nblocks = xblocks;
+    if (dot)
+      k_xinv<R, true><<<xblocks, kXThreads, xsm, st>>>(w.spec, out, self ? nullptr : dot_with, w.partials, g, w.qx,
+                                                       w.px, w.tw[0], scale, self);
+    else
+      k_xinv<R, false><<<xblocks, kXThreads, xsm, st>>>(w.spec, out, nullptr, nullptr, g, w.qx, w.px, w.tw[0],
+                                                        scale, false);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return e;
   ++nl;
+  if (dot) {
+    e = reduce_partials(w.partials, nblocks, 1, dot_out, st, &nl);
+    if (e != cudaSuccess) return e;
+  }
   if (nlaunch) *nlaunch += nl;
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 template cudaError_t spectral_setup<float>(const GridDesc&, SpecWork<float>&);
@@ -497,7 +474,7 @@ template cudaError_t spectral_apply<float>(const GridDesc&, SpecWork<float>&, co
                                            const uint8_t*, const float*, XIn, float*, const float*, double*,
                                            cudaStream_t, long long*);
 template cudaError_t spectral_apply<double>(const GridDesc&, SpecWork<double>&, const MatTable<double>&,
-                                            const double*, const uint8_t*, const float*, XIn, double*,
+                                            const double*, const uint8_t*, const double*, XIn, double*,
                                             const double*, double*, cudaStream_t, long long*);
 
 }  // namespace rve

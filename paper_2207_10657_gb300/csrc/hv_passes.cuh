@@ -36,7 +36,7 @@ enum class XIn { Plain = 0, Tangent = 1 };
 // launches issued is added to *nlaunch.
 template <typename R>
 cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>& mt, const R* in,
-                           const uint8_t* phase, const float* damage, XIn mode, R* out,
+                           const uint8_t* phase, const R* damage, XIn mode, R* out,
                            const R* dot_with, double* dot_out, cudaStream_t st, long long* nlaunch);
 
 template <typename R>

@@ -43,7 +43,7 @@ struct Impl {
   uint8_t* phase = nullptr;
   R *eps = nullptr, *sig = nullptr, *sig_t = nullptr, *g = nullptr, *z = nullptr, *r = nullptr, *d = nullptr,
     *Hd = nullptr, *tmp = nullptr;
-  float *D = nullptr, *D_t = nullptr, *kap = nullptr, *kap_t = nullptr, *khist = nullptr;
+  R *D = nullptr, *D_t = nullptr, *kap = nullptr, *kap_t = nullptr, *khist = nullptr;
   DevScalars* S = nullptr;
 };
 
@@ -123,7 +123,7 @@ rve_status create_impl(rve_ctx* c, const uint8_t* phase_ids, const rve_phase* ph
   m->mt.nphase = nphase;
   for (int i = 0; i < kMaxPhases; ++i) {
     m->mt.lam[i] = m->mt.mu[i] = 0;
-    m->mt.kappa0[i] = m->mt.kappaf[i] = 0.f;
+    m->mt.kappa0[i] = m->mt.kappaf[i] = 0;
     m->mt.damaging[i] = 0;
   }
   for (int i = 0; i < nphase; ++i) {
@@ -131,16 +131,16 @@ rve_status create_impl(rve_ctx* c, const uint8_t* phase_ids, const rve_phase* ph
     m->mt.lam[i] = (R)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
     m->mt.mu[i] = (R)(E / (2.0 * (1.0 + nu)));
     m->mt.damaging[i] = phases[i].damaging ? 1 : 0;
-    m->mt.kappa0[i] = (float)phases[i].kappa0;
-    m->mt.kappaf[i] = (float)phases[i].kappaf;
+    m->mt.kappa0[i] = (R)phases[i].kappa0;
+    m->mt.kappaf[i] = (R)phases[i].kappaf;
   }
   CK(spectral_setup<R>(g, m->sw), "spectral setup");
   const size_t nf = (size_t)g.ncomp * g.nvox * sizeof(R);
-  const size_t ns = (size_t)g.nvox * sizeof(float);
+  const size_t ns = (size_t)g.nvox * sizeof(R);
   R** fields[] = {&m->eps, &m->sig, &m->sig_t, &m->g, &m->z, &m->r, &m->d, &m->Hd, &m->tmp};
   for (R** f : fields) CK(cudaMalloc(f, nf), "field allocation");
-  float** sf[] = {&m->D, &m->D_t, &m->kap, &m->kap_t, &m->khist};
-  for (float** f : sf) CK(cudaMalloc(f, ns), "scalar-field allocation");
+  R** sf[] = {&m->D, &m->D_t, &m->kap, &m->kap_t, &m->khist};
+  for (R** f : sf) CK(cudaMalloc(f, ns), "scalar-field allocation");
   CK(cudaMalloc(&m->phase, g.nvox), "phase allocation");
   CK(cudaMalloc(&m->S, sizeof(DevScalars)), "scalar allocation");
   CK(cudaMemsetAsync(m->S, 0, sizeof(DevScalars), c->st), "memset");
@@ -284,22 +284,22 @@ rve_status solve_step_impl(rve_ctx* c, const double dE[6], const void* init, rve
   rp->converged = converged ? 1 : 0;
   if (!converged) return fail(c, RVE_ERR_NOT_CONVERGED, "load step did not converge within max_nr");
   // commit history: kappa_n <- max(kappa_n, kappa(eps)) (kap already holds the max)
-  CK(cudaMemcpyAsync(m->khist, m->kap, (size_t)g.nvox * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "commit");
+  CK(cudaMemcpyAsync(m->khist, m->kap, (size_t)g.nvox * sizeof(R), cudaMemcpyDeviceToDevice, c->st), "commit");
   CK(cudaStreamSynchronize(c->st), "synchronize");
   return RVE_OK;
 }
 
 template <typename R>
-rve_status set_state_impl(rve_ctx* c, const void* strain, const float* khist) {
+rve_status set_state_impl(rve_ctx* c, const void* strain, const void* khist) {
   Impl<R>* m = impl_of<R>(c);
   const GridDesc& g = c->g;
   CK(cudaMemcpyAsync(m->eps, strain, (size_t)g.ncomp * g.nvox * sizeof(R), cudaMemcpyDeviceToDevice, c->st),
      "state copy");
   if (khist)
-    CK(cudaMemcpyAsync(m->khist, khist, (size_t)g.nvox * sizeof(float), cudaMemcpyDeviceToDevice, c->st),
+    CK(cudaMemcpyAsync(m->khist, khist, (size_t)g.nvox * sizeof(R), cudaMemcpyDeviceToDevice, c->st),
        "history copy");
   else
-    CK(cudaMemsetAsync(m->khist, 0, (size_t)g.nvox * sizeof(float), c->st), "history reset");
+    CK(cudaMemsetAsync(m->khist, 0, (size_t)g.nvox * sizeof(R), c->st), "history reset");
   CK(trial_eval<R>(g, m->mt, m->phase, m->eps, nullptr, m->khist, nullptr, nullptr, m->sig, m->D, m->kap, m->S,
                    m->sw.partials, c->st, &c->launches),
      "state stress");
@@ -307,10 +307,10 @@ rve_status set_state_impl(rve_ctx* c, const void* strain, const float* khist) {
 }
 
 template <typename R>
-rve_status get_state_impl(rve_ctx* c, void* strain, float* kappa, void* stress, float* damage) {
+rve_status get_state_impl(rve_ctx* c, void* strain, void* kappa, void* stress, void* damage) {
   Impl<R>* m = impl_of<R>(c);
   const GridDesc& g = c->g;
-  const size_t nf = (size_t)g.ncomp * g.nvox * sizeof(R), ns = (size_t)g.nvox * sizeof(float);
+  const size_t nf = (size_t)g.ncomp * g.nvox * sizeof(R), ns = (size_t)g.nvox * sizeof(R);
   if (strain) CK(cudaMemcpyAsync(strain, m->eps, nf, cudaMemcpyDeviceToDevice, c->st), "copy");
   if (stress) CK(cudaMemcpyAsync(stress, m->sig, nf, cudaMemcpyDeviceToDevice, c->st), "copy");
   if (kappa) CK(cudaMemcpyAsync(kappa, m->khist, ns, cudaMemcpyDeviceToDevice, c->st), "copy");
@@ -424,22 +424,23 @@ rve_status rve_create(const int dims[3], int ndim, const uint8_t* phase_ids_dev,
 
 #define DISPATCH(c, fn, ...) ((c)->precision == 32 ? fn<float>(c, __VA_ARGS__) : fn<double>(c, __VA_ARGS__))
 
-rve_status rve_set_state(rve_t c, const void* strain, const float* khist) {
+rve_status rve_set_state(rve_t c, const void* strain, const void* khist) {
   if (!c) return RVE_ERR_ARG;
   if (!strain) return fail(c, RVE_ERR_ARG, "strain is NULL");
   return DISPATCH(c, set_state_impl, strain, khist);
 }
 
-rve_status rve_get_state(rve_t c, void* strain, float* kappa, void* stress, float* damage) {
+rve_status rve_get_state(rve_t c, void* strain, void* kappa, void* stress, void* damage) {
   if (!c) return RVE_ERR_ARG;
   return DISPATCH(c, get_state_impl, strain, kappa, stress, damage);
 }
 
-rve_status rve_set_damage(rve_t c, const float* damage) {
+rve_status rve_set_damage(rve_t c, const void* damage) {
   if (!c) return RVE_ERR_ARG;
   if (!damage) return fail(c, RVE_ERR_ARG, "damage is NULL");
-  float* D = c->precision == 32 ? impl_of<float>(c)->D : impl_of<double>(c)->D;
-  CK(cudaMemcpyAsync(D, damage, (size_t)c->g.nvox * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "damage copy");
+  void* D = c->precision == 32 ? (void*)impl_of<float>(c)->D : (void*)impl_of<double>(c)->D;
+  const size_t es = c->precision == 32 ? sizeof(float) : sizeof(double);
+  CK(cudaMemcpyAsync(D, damage, (size_t)c->g.nvox * es, cudaMemcpyDeviceToDevice, c->st), "damage copy");
   return RVE_OK;
 }
 

@@ -228,8 +228,8 @@ __global__ void __launch_bounds__(kVThreads)
 template <typename R>
 __global__ void __launch_bounds__(kVThreads)
     k_trial(const GridDesc g, const MatTable<R> mt, const uint8_t* __restrict__ phase, const R* __restrict__ eps,
-            const R* __restrict__ p, const float* __restrict__ khist, const R* __restrict__ sig0,
-            const float* __restrict__ D0, R* __restrict__ sig_t, float* __restrict__ D_t, float* __restrict__ kap_t,
+            const R* __restrict__ p, const R* __restrict__ khist, const R* __restrict__ sig0,
+            const R* __restrict__ D0, R* __restrict__ sig_t, R* __restrict__ D_t, R* __restrict__ kap_t,
             double* __restrict__ part) {
   const int nc = g.ncomp, nd = g.ndim;
   const long long nv = g.nvox;
@@ -243,18 +243,18 @@ __global__ void __launch_bounds__(kVThreads)
     const int ph = phase[v];
     const R lam = mt.lam[ph], mu = mt.mu[ph];
     R D = 0;
-    float kap = 0.f;
+    R kap = 0;
     if (mt.damaging[ph]) {
       const R kt = kappa_tension<R>(e, nd);
-      const float kh = khist ? khist[v] : 0.f;
-      const R k = fmax((R)kh, kt);
-      kap = (float)k;
-      D = damage_of<R>(k, (R)mt.kappa0[ph], (R)mt.kappaf[ph]);
+      const R kh = khist ? khist[v] : (R)0;
+      const R k = fmax(kh, kt);
+      kap = k;
+      D = damage_of<R>(k, mt.kappa0[ph], mt.kappaf[ph]);
     }
     const R keep = (R)1 - D;
     R tr = 0, trp = 0;
     for (int i = 0; i < nd; ++i) { tr += e[i]; trp += pv[i]; }
-    const R keep0 = D0 ? (R)1 - (R)D0[v] : (R)1;
+    const R keep0 = D0 ? (R)1 - D0[v] : (R)1;
     for (int c = 0; c < nc; ++c) {
       const R s = keep * ((R)2 * mu * e[c] + (c < nd ? lam * tr : (R)0));
       sig_t[c * nv + v] = s;
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kVThreads)
       acc[4].add(pv[c] * pv[c]);
       acc[5].add(e[c] * e[c]);
     }
-    if (D_t) D_t[v] = (float)D;
+    if (D_t) D_t[v] = D;
     if (kap_t) kap_t[v] = kap;
   }
   finish_sums<R, 6>(acc, part);
@@ -383,7 +383,7 @@ cudaError_t cg_dupdate(const GridDesc& g, const R* z, const R* r, R* d, DevScala
 
 template <typename R>
 cudaError_t trial_eval(const GridDesc& g, const MatTable<R>& mt, const uint8_t* phase, const R* eps, const R* p,
-                       const float* khist, const R* sig0, const float* D0, R* sig_t, float* D_t, float* kap_t,
+                       const R* khist, const R* sig0, const R* D0, R* sig_t, R* D_t, R* kap_t,
                        DevScalars* S, double* part, cudaStream_t st, long long* nl) {
   k_trial<R><<<kVBlocks, kVThreads, 0, st>>>(g, mt, phase, eps, p, khist, sig0, D0, sig_t, D_t, kap_t, part);
   RVE_TRY(cudaGetLastError());
@@ -432,7 +432,7 @@ cudaError_t field_means(const GridDesc& g, const R* sig, const R* eps, DevScalar
   template cudaError_t cg_dupdate<R>(const GridDesc&, const R*, const R*, R*, DevScalars*, double*,            \
                                      cudaStream_t, long long*);                                                 \
   template cudaError_t trial_eval<R>(const GridDesc&, const MatTable<R>&, const uint8_t*, const R*, const R*,   \
-                                     const float*, const R*, const float*, R*, float*, float*, DevScalars*,     \
+                                     const R*, const R*, const R*, R*, R*, R*, DevScalars*,                     \
                                      double*, cudaStream_t, long long*);                                        \
   template cudaError_t axpy<R>(long long, R, const R*, R*, cudaStream_t, long long*);                          \
   template cudaError_t add_uniform<R>(const GridDesc&, R*, const double*, cudaStream_t, long long*);           \

@@ -73,7 +73,7 @@ cudaError_t cg_dupdate(const GridDesc& g, const R* z, const R* r, R* d, DevScala
 // kappa_t, and group T sums against the stored state (sig0, D0, may be NULL).
 template <typename R>
 cudaError_t trial_eval(const GridDesc& g, const MatTable<R>& mt, const uint8_t* phase, const R* eps, const R* p,
-                       const float* khist, const R* sig0, const float* D0, R* sig_t, float* D_t, float* kap_t,
+                       const R* khist, const R* sig0, const R* D0, R* sig_t, R* D_t, R* kap_t,
                        DevScalars* S, double* part, cudaStream_t st, long long* nl);
 // rho_bar, radius update and acceptance (1 thread).
 cudaError_t tr_decide(DevScalars* S, cudaStream_t st, long long* nl);

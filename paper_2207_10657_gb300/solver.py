@@ -72,11 +72,11 @@ class RVESolver:
         return t
 
     def scalar_field(self):
-        return torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        return torch.empty(self.shape, dtype=self.dtype, device=self.device)
 
     def _chk(self, t, kind="field"):
         want = (self.ncomp,) + self.shape if kind == "field" else self.shape
-        dt = self.dtype if kind == "field" else torch.float32
+        dt = self.dtype
         if t.device != self.device or t.dtype != dt or tuple(t.shape) != want or not t.is_contiguous():
             raise ValueError(f"expected contiguous {dt} {kind} of shape {want} on {self.device}, "
                              f"got {t.dtype} {tuple(t.shape)} on {t.device}")

@@ -37,8 +37,11 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+# generic-engine sizes, the compile-time-specialised FP32 sizes (32..512,
+# 96/192/384) and mixtures of both, degenerate 2-point axes and a 1024 axis
 GRIDS = [(32, 24), (30, 40), (2, 2), (1024, 8), (8, 12, 10), (16, 16, 16), (24, 20, 18), (2, 2, 2),
-         (6, 4, 1024)]
+         (6, 4, 1024), (96, 64), (512, 32), (32, 32, 32), (64, 32, 96), (128, 192, 8), (384, 6, 4),
+         (8, 10, 512)]
 
 
 @pytest.mark.parametrize("precision", [32, 64])
@@ -59,7 +62,8 @@ def test_project_matches_oracle(dims, precision):
 
 
 @pytest.mark.parametrize("precision", [32, 64])
-@pytest.mark.parametrize("dims", [(32, 24), (64, 30), (8, 12, 10), (16, 16, 16), (24, 20, 18), (40, 36, 12)])
+@pytest.mark.parametrize("dims", [(32, 24), (64, 30), (8, 12, 10), (16, 16, 16), (24, 20, 18), (40, 36, 12),
+                                  (64, 64), (256, 96), (32, 32, 32), (64, 96, 32), (128, 64, 64)])
 def test_hessp_matches_oracle(dims, precision):
     nd = len(dims)
     nc = 3 if nd == 2 else 6
@@ -69,7 +73,7 @@ def test_hessp_matches_oracle(dims, precision):
         pm = random_spheres(dims, count=5, rmin=1.5, rmax=3.5, seed=4)
     D = damage_snapshot(pm, dmax=0.9, seed=1)
     s = _solver(dims, pm, [MATRIX, STIFF], precision)
-    s.set_damage(torch.from_numpy(D).cuda())
+    s.set_damage(_to_dev(D, precision))
     v = random_field(nc, dims, seed=2)
     out = s.hessp(_to_dev(v, precision)).cpu().numpy()
     ref = _oracle_rve(pm, [MATRIX, STIFF]).hessp(D.astype(np.float64), v)
@@ -82,7 +86,7 @@ def test_hessp_matches_oracle(dims, precision):
 
 
 @pytest.mark.parametrize("precision", [32, 64])
-@pytest.mark.parametrize("dims", [(32, 32), (12, 16, 10)])
+@pytest.mark.parametrize("dims", [(32, 32), (12, 16, 10), (32, 32, 32)])
 def test_state_stress_damage_and_energy(dims, precision):
     """Constitutive update (Appendix A) and the first-order incremental energy
     (Eq. (18)) against the oracle."""
@@ -91,12 +95,14 @@ def test_state_stress_damage_and_energy(dims, precision):
     pm = circular_inclusion(dims, 0.3) if nd == 2 else random_spheres(dims, count=3, rmin=1.5, rmax=3.0, seed=5)
     rng = np.random.default_rng(3)
     eps = rng.standard_normal((nc,) + pm.shape) * 4e-4
-    kh = rng.uniform(0, 6e-4, pm.shape).astype(np.float32)
+    kh = rng.uniform(0, 6e-4, pm.shape)
+    if precision == 32:
+        kh = kh.astype(np.float32).astype(np.float64)
     s = _solver(dims, pm, [MATRIX, STIFF], precision)
-    s.set_state(_to_dev(eps, precision), torch.from_numpy(kh).cuda())
+    s.set_state(_to_dev(eps, precision), _to_dev(kh, precision))
     st = s.get_state()
     orv = _oracle_rve(pm, [MATRIX, STIFF])
-    sig, D, kap = orv.stress(eps, kh.astype(np.float64))
+    sig, D, kap = orv.stress(eps, kh)
     # damage: identical except within 1e-3 of the threshold kappa0
     near = np.abs(kap - 1e-4) <= 1e-3 * 1e-4
     dg = st["damage"].cpu().numpy()
@@ -104,7 +110,7 @@ def test_state_stress_damage_and_energy(dims, precision):
     assert _rel(st["sigma"].cpu().numpy(), sig) < 20 * TOL[precision]
     p = rng.standard_normal((nc,) + pm.shape) * 2e-4
     dW, dm, grad = s.energy_grad(_to_dev(p, precision))
-    sig_t, _, _ = orv.stress(eps + p, kh.astype(np.float64))
+    sig_t, _, _ = orv.stress(eps + p, kh)
     dW_ref = 0.5 * (np.sum(sig * p) + np.sum(sig_t * p))
     dm_ref = np.sum(sig * p) + 0.5 * np.sum(p * orv.tangent(D, p))
     tol = 1e-5 if precision == 32 else 1e-11
@@ -150,7 +156,14 @@ def test_load_path_2d_plane_strain_fp64():
     kap_gpu = st["kappa"].cpu().numpy()
     dmg_ref = ref["kappa"] > 1e-4
     near = np.abs(ref["kappa"] - 1e-4) <= 1e-3 * 1e-4
-    assert np.array_equal((kap_gpu > 1e-4)[~near], dmg_ref[~near])
+    # The centred disc and the uniaxial load are symmetric under x and y
+    # mirrors (voxel i <-> N-1-i), so a localised band may form on either
+    # mirror side: the damaged set is unique only up to that group.
+    dg = kap_gpu > 1e-4
+    images = [dg, dg[:, ::-1], dg[::-1, :], dg[::-1, ::-1]]
+    nimg = [near, near[:, ::-1], near[::-1, :], near[::-1, ::-1]]
+    assert any(np.array_equal(im[~(nr | near)], dmg_ref[~(nr | near)]) for im, nr in zip(images, nimg)), \
+        (int(dg.sum()), int(dmg_ref.sum()))
     s.close()
 
 
@@ -233,7 +246,7 @@ def test_full_size_256_plane_wave_and_symmetry():
         scale = max(np.linalg.norm(ref), 1e-3 * np.linalg.norm(field))
         assert np.linalg.norm(out - ref) / scale < 5e-6, k
         del field, out, ref
-    s.set_damage(torch.from_numpy(D).cuda())
+    s.set_damage(_to_dev(D, 32))
     u = s.project(_to_dev(random_field(6, dims, seed=5, dtype=np.float32), 32))
     w = s.project(_to_dev(random_field(6, dims, seed=6, dtype=np.float32), 32))
     Hu, Hw = s.hessp(u), s.hessp(w)

@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of the trust-region / Steihaug-CG homogenisation solver on one GB300.
+
+Workload (N=1): the 256^3 random-sphere RVE -- 144 non-overlapping spheres,
+radius U[4, 10] voxels, seed 0, stiff elastic spheres (E=10, nu=0.2) in a
+damaging matrix (E=1, nu=0.3, kappa0=1e-4, kappaf=1e-3) -- under uniaxial
+mean strain eps_zz ramped in increments of 5e-5 (2e-3 over 40 increments),
+the other five mean components stress-free.  FP32 fields, FP64 reductions,
+relative residual |G:sigma|/|sigma| <= 1e-6.
+
+A bench *step* is one load increment (Algorithm 2) from a fixed reference
+state (the unloaded cell, reset with rve_set_state at the start of every
+step, which re-evaluates the constitutive law): uniform predictor,
+constitutive update, gradient, and trust-region Newton iterations, each one
+a Steihaug-CG solve (Hessian-vector products: tangent + forward FFT +
+projection + inverse FFT, CG reductions and updates) followed by the trial
+constitutive evaluation, the first-order incremental-energy ratio test and
+the new gradient.  value = voxels x Hessian-vector products / time (all
+ranks), ms_per_step = the load-step time.  The first increment stays below
+the damage threshold; later increments localise a crack band and take
+10^4-10^5 products each, too long for a bench run of minutes.
+
+Roofline: the dominant kernel's average launch time comes from CUDA events
+recorded by the library around every launch inside the timed region;
+algorithmic bytes per launch are the compulsory reads + writes of that pass.
+
+--impl reference times the FP64 CPU oracle (the repo's plain restatement of
+the method, single thread): each step is one Hessian-vector product on a
+bounded sample of the workload, the 128^3 cell of the same sphere model
+(48 spheres) with a damage snapshot D ~ U[0, 0.9] on the matrix, so that
+--steps 10 --warmup 3 ends within a few minutes.  The GPU arm's cpu_baseline
+times one oracle product on the full 256^3 cell.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel-Hv/s at 256³ (% HBM roofline); load-step time, warm start vs plain @1e-6"
+UNIT = "voxel-Hv/s"
+N = 256
+INC = 5e-5
+MATRIX = (1.0, 0.3, True, 1e-4, 1e-3)
+STIFF = (10.0, 0.2, False, 0.0, 0.0)
+FREE = [1, 1, 0, 1, 1, 1]
+WORKLOAD = ("256^3 random-sphere RVE (144 spheres, r~U[4,10], seed 0; spheres E=10 nu=0.2 elastic, matrix "
+            "E=1 nu=0.3 damaging kappa0=1e-4 kappaf=1e-3), uniaxial eps_zz increments 5e-5 (40 to 2e-3), "
+            "other components stress-free, trust-region Newton + Steihaug CG to rel. residual 1e-6")
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--n", type=int, default=N, help="grid size (default 256)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2207_10657_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel, n):
+    """DRAM bytes per launch of `kernel` at size n from the committed ncu
+    summary, or None if absent or taken on different kernel sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("kernel_hash") != _kernel_hash():
+        return None
+    rec = d.get("kernels", {}).get(f"{kernel}@{n}")
+    return None if rec is None else rec.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------ CPU oracle
+def _oracle_hv_setup(n):
+    import numpy as np
+    import oracle
+    from synth import random_spheres, damage_snapshot, random_field
+    dims = (n, n, n)
+    pm = random_spheres(dims, count=144 if n >= 256 else 48, rmin=4.0, rmax=10.0, seed=0)
+    D = damage_snapshot(pm, dmax=0.9, seed=1).astype(np.float64)
+    v = random_field(6, dims, seed=2)
+    rve = oracle.RVE(pm, [oracle.Phase(1.0, 0.3, True, 1e-4, 1e-3), oracle.Phase(10.0, 0.2)])
+    return rve, D, v
+
+
+def _oracle_hv_time(n, reps=1):
+    rve, D, v = _oracle_hv_setup(n)
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        rve.hessp(D, v)
+        ts.append(time.perf_counter() - t0)
+    return ts
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(var, "1")
+    n = min(args.n, 128)
+    rve, D, v = _oracle_hv_setup(n)
+    for _ in range(args.warmup):
+        rve.hessp(D, v)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rve.hessp(D, v)
+    dt = time.perf_counter() - t0
+    val = args.steps * n ** 3 / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [n, n, n]},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one FP64 Hessian-vector product per step on the {n}^3 cell of the same "
+                                   "sphere model (damage snapshot D~U[0,0.9] on the matrix), numpy, 1 thread"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ GPU arm
+def _pass_bytes(n, pass_name):
+    """Algorithmic (compulsory) DRAM bytes of one launch of a pass at n^3, FP32."""
+    nvox = n ** 3
+    spec = 6 * n * n * (n // 2 + 1) * 8  # half spectrum, 6 complex components
+    field = 6 * nvox * 4
+    return {
+        "xfwd_tangent": field + nvox * (1 + 4) + spec,
+        "y_fwd": 2 * spec,
+        "z_proj": 2 * spec,
+        "y_inv": 2 * spec,
+        "x_inv": spec + field,
+        "trial": nvox * (24 + 24 + 4 + 24 + 4 + 1 + 24 + 4 + 4),
+        "cg_vec": nvox * 120,
+    }.get(pass_name)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+    torch.cuda.set_device(local)
+    from paper_2207_10657_gb300 import build as _build
+    if rank == 0:
+        _build.build()
+    if dist:
+        dist.barrier()
+    from paper_2207_10657_gb300 import RVESolver, binding
+    from synth import random_spheres
+
+    n = args.n
+    dims = (n, n, n)
+    nvox = n ** 3
+    pm = random_spheres(dims, count=144 if n >= 256 else 48, rmin=4.0, rmax=10.0, seed=0)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, stream=st, eta_eq=1e-6, eta_cg=1e-2, max_nr=400)
+    dE = [0.0, 0.0, INC, 0.0, 0.0, 0.0]
+    eps0 = s.field(0.0)  # reference state: the unloaded cell
+
+    def step():
+        s.set_state(eps0)
+        return s.solve_step(dE, free_mask=FREE, raise_on_error=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---------------- timed region: K load steps (device-resident inputs)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    binding.rve_pass_timing(s.h, True)
+    hv0, l0 = s.hv_count, s.launch_count
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(st)
+    timed = []
+    for _ in range(args.steps):
+        timed.append(step())
+    ev1.record(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop() if sampler else None
+    hv = s.hv_count - hv0
+    launches = s.launch_count - l0
+    stats = binding.rve_pass_stats(s.h)
+    binding.rve_pass_timing(s.h, False)
+    t_loc = torch.tensor([ms, float(hv)], dtype=torch.float64, device="cuda")
+    if dist:
+        tmax = t_loc.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        hsum = t_loc.clone()
+        dist.all_reduce(hsum[1:], op=dist.ReduceOp.SUM)
+        ms_max, hv_all = float(tmax[0]), float(hsum[1])
+    else:
+        ms_max, hv_all = ms, float(hv)
+    value = hv_all * nvox / (ms_max / 1e3)
+
+    # ---------------- end to end through the public API with host buffers:
+    # per step, the reference strain field is copied from pinned host memory,
+    # the load step runs (dE is a host argument of rve_solve_step), and the
+    # converged strain field is read back to pinned host memory.
+    host_in = torch.zeros((6,) + pm.shape, dtype=torch.float32).pin_memory()
+    host_out = torch.empty((6,) + pm.shape, dtype=torch.float32).pin_memory()
+    dev_in = s.field()
+    dev_out = s.field()
+    e2e_steps = max(1, args.steps)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    hv_e0 = s.hv_count
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(st):
+            dev_in.copy_(host_in, non_blocking=True)
+        s.set_state(dev_in)
+        s.solve_step(dE, free_mask=FREE, raise_on_error=False)
+        binding.rve_get_state(s.h, dev_out.data_ptr())
+        with torch.cuda.stream(st):
+            host_out.copy_(dev_out, non_blocking=True)
+        st.synchronize()
+    e2e_s = time.perf_counter() - t0
+    hv_e = s.hv_count - hv_e0
+    e2e_val = hv_e * nvox / e2e_s
+    if dist:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_val = hv_e * nvox * ws / float(tt[0])
+
+    # ---------------- roofline of the dominant pass
+    dom = max((k for k in stats if stats[k][0] > 0), key=lambda k: stats[k][1])
+    cnt, tot = stats[dom]
+    avg_s = tot / cnt / 1e3
+    bytes_launch = _pass_bytes(n, dom)
+    peak, peak_kind = _peaks()
+    achieved = bytes_launch / avg_s / 1e9
+    traffic = _traffic(dom, n)
+    hv_only_ms = sum(stats[k][1] for k in ("xfwd_tangent", "y_fwd", "z_proj", "y_inv", "x_inv"))
+    nprod = max(stats["z_proj"][0], 1)
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        # bounded oracle sample on the host cores (one FP64 Hv of the same workload)
+        try:
+            for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+                os.environ.setdefault(var, "1")
+            ts = _oracle_hv_time(n, reps=1)
+            cpu = {"value": nvox / ts[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"one FP64 Hessian-vector product of the {n}^3 workload (damage snapshot "
+                             f"D~U[0,0.9]), numpy, 1 thread, {ts[0]:.1f} s"}
+        except Exception as ex:  # report, do not hide
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [n, n, n], "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (each 6-component FP32 field is 403 MB > 129 MB L2)",
+                   "hv_per_step": hv / args.steps,
+                   "nr_iters_per_step": [r["nr_iters"] for r in timed],
+                   "cg_iters_per_step": [r["cg_iters"] for r in timed],
+                   "converged": [r["converged"] for r in timed],
+                   "mean_stress_zz": [r["mean_stress"][2] for r in timed],
+                   "hv_only_ms": hv_only_ms / nprod,
+                   "hv_only_voxel_hv_per_s": nvox / (hv_only_ms / nprod / 1e3),
+                   "pass_ms_per_launch": {k: (v[1] / v[0] if v[0] else None) for k, v in stats.items()}},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": bytes_launch},
+        "compulsory_fraction": {"bytes_per_voxel": 53, "frac": 53 * nvox / (hv_only_ms / nprod / 1e3) / 1e9 / peak},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 6 * nvox * 4,
+                "d2h_bytes_per_step": 6 * nvox * 4},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    s.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

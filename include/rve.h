@@ -157,6 +157,20 @@ rve_status rve_energy_grad(rve_t, const void* p_dev, double* dW_bar_host, double
 rve_status rve_solve_step(rve_t, const double dE_host[6], const uint8_t free_mask_host[6],
                           const void* init_incr_dev, rve_step_report* rep_host);
 
+/* Per-pass device timing, for benchmarks (not part of the method).
+ * Pass ids: 0 x-forward FFT with the fused tangent, 1 y-forward FFT,
+ * 2 z-FFT + projection + inverse z-FFT, 3 y-inverse FFT, 4 x-inverse FFT,
+ * 5 2D y-FFT + projection + inverse, 6 constitutive trial evaluation,
+ * 7 CG vector updates.  rve_pass_timing(h, 1) starts (and resets) the
+ * recording of CUDA events on the context's stream around every launch of
+ * those kernels (up to 8192 launches; later ones are not timed);
+ * rve_pass_timing(h, 0) stops it.  rve_pass_stats synchronises on the last
+ * event and writes, for pass ids 0..n-1, the number of timed launches and
+ * their summed device time in milliseconds. */
+#define RVE_NPASS 8
+rve_status rve_pass_timing(rve_t, int enable);
+rve_status rve_pass_stats(rve_t, long long* counts_host, double* ms_host, int n);
+
 /* Message of the last error on this context (static storage; never NULL). */
 const char* rve_last_error(rve_t);
 

@@ -60,6 +60,9 @@ _SIGS = [
     ("rve_solve_step", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_uint8), ctypes.c_void_p,
                                       ctypes.POINTER(rve_step_report)]),
+    ("rve_pass_timing", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("rve_pass_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     ("rve_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("rve_hv_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("rve_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
@@ -155,6 +158,21 @@ def rve_solve_step(h, dE, free_mask=None, init_ptr=0, raise_on_error=True):
     if raise_on_error:
         check(st, h)
     return st, rep
+
+
+PASS_NAMES = ["xfwd_tangent", "y_fwd", "z_proj", "y_inv", "x_inv", "y_proj_2d", "trial", "cg_vec"]
+
+
+def rve_pass_timing(h, enable=True):
+    check(lib().rve_pass_timing(h, 1 if enable else 0), h)
+
+
+def rve_pass_stats(h):
+    n = len(PASS_NAMES)
+    counts = (ctypes.c_longlong * n)()
+    ms = (ctypes.c_double * n)()
+    check(lib().rve_pass_stats(h, counts, ms, n), h)
+    return {PASS_NAMES[i]: (counts[i], ms[i]) for i in range(n)}
 
 
 def rve_last_error(h):

@@ -387,6 +387,8 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
   const size_t xsm = (size_t)((g.ncomp * w.qx) / 2) * g.nx * sizeof(C);
   // x forward (tangent fused)
   e = cudaErrorNotSupported;
+  {
+  PassScope ps(w.timer, st, PASS_XFWD);
   if constexpr (F32) {
     if (fast_size(g.nx))
       e = fast_xfwd(g, in, phase, damage, mt, w.spec, w.tw[0], mode == XIn::Tangent, st);
@@ -398,6 +400,7 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
       k_xfwd<R, 0><<<xblocks, kXThreads, xsm, st>>>(in, phase, damage, mt, w.spec, g, w.qx, w.px, w.tw[0]);
     e = cudaGetLastError();
   }
+  }
   if (e != cudaSuccess) return e;
   ++nl;
   if (g.ndim == 3) {
@@ -407,6 +410,7 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
     const size_t zsm = (size_t)6 * w.tz * g.nz * sizeof(C);
     for (int pass = 0; pass < 3; ++pass) {
       e = cudaErrorNotSupported;
+      PassScope ps(w.timer, st, pass == 0 ? PASS_YFWD : (pass == 1 ? PASS_ZPROJ : PASS_YINV));
       if constexpr (F32) {
         if (pass != 1 && fast_size(g.ny)) e = fast_ycols(g, w.spec, w.tw[1], pass == 2, st);
         if (pass == 1 && fast_size(g.nz)) e = fast_zproj(g, w.spec, w, st);
@@ -424,6 +428,7 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
     }
   } else {
     e = cudaErrorNotSupported;
+    PassScope ps(w.timer, st, PASS_YPROJ2D);
     if constexpr (F32) {
       if (fast_size(g.ny)) e = fast_yproj2d(g, w.spec, w, st);
     }
@@ -442,6 +447,8 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
   const bool self = dot && (dot_with == out);
   int nblocks = xblocks;
   e = cudaErrorNotSupported;
+  {
+  PassScope ps(w.timer, st, PASS_XINV);
   if constexpr (F32) {
     if (fast_size(g.nx))
       e = fast_xinv(g, w.spec, out, self ? nullptr : dot_with, w.partials, w.tw[0], dot, self, &nblocks, st);
@@ -455,6 +462,7 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
       k_xinv<R, false><<<xblocks, kXThreads, xsm, st>>>(w.spec, out, nullptr, nullptr, g, w.qx, w.px, w.tw[0],
                                                         scale, false);
     e = cudaGetLastError();
+  }
   }
   if (e != cudaSuccess) return e;
   ++nl;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "pass_timer.cuh"
 
 namespace rve {
 
@@ -28,6 +29,7 @@ template <typename R> struct SpecWork {
   int tz;   // kx columns per z-pass / 2D y-pass block
   double* partials = nullptr;  // per-block FP64 partial sums (epilogues)
   int max_partials = 0;
+  PassTimer* timer = nullptr;  // optional per-pass event timing
 };
 
 enum class XIn { Plain = 0, Tangent = 1 };

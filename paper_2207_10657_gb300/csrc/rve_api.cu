@@ -68,6 +68,7 @@ struct rve_ctx {
   double R = 0.0, Rmax = 0.0;
   unsigned free_mask = 0;
   DevScalars* Sh = nullptr;  // pinned host mirror
+  PassTimer timer;
   void* impl = nullptr;
 };
 
@@ -135,6 +136,7 @@ rve_status create_impl(rve_ctx* c, const uint8_t* phase_ids, const rve_phase* ph
     m->mt.kappaf[i] = (R)phases[i].kappaf;
   }
   CK(spectral_setup<R>(g, m->sw), "spectral setup");
+  m->sw.timer = &c->timer;
   const size_t nf = (size_t)g.ncomp * g.nvox * sizeof(R);
   const size_t ns = (size_t)g.nvox * sizeof(R);
   R** fields[] = {&m->eps, &m->sig, &m->sig_t, &m->g, &m->z, &m->r, &m->d, &m->Hd, &m->tmp};
@@ -182,7 +184,10 @@ rve_status steihaug(rve_ctx* c, rve_step_report* rep) {
     ++c->hv;
     if (rep) ++rep->hv_products;
     CK(cg_alpha(m->S, c->st, nl), "cg alpha");
-    CK(cg_update<R>(g, m->z, m->r, m->d, m->Hd, m->S, m->sw.partials, c->st, nl), "cg update");
+    {
+      PassScope ps(&c->timer, c->st, PASS_CGVEC);
+      CK(cg_update<R>(g, m->z, m->r, m->d, m->Hd, m->S, m->sw.partials, c->st, nl), "cg update");
+    }
     CK(cg_beta(m->S, c->st, nl), "cg beta");
     s = read_scalars<R>(c);
     if (s != RVE_OK) return s;
@@ -194,7 +199,10 @@ rve_status steihaug(rve_ctx* c, rve_step_report* rep) {
       if (rep) ++rep->hv_products;
       CK(cg_restart<R>(g, m->r, m->tmp, m->g, m->S, m->sw.partials, c->st, nl), "cg restart");
     }
-    CK(cg_dupdate<R>(g, m->z, m->r, m->d, m->S, m->sw.partials, c->st, nl), "cg direction");
+    {
+      PassScope ps(&c->timer, c->st, PASS_CGVEC);
+      CK(cg_dupdate<R>(g, m->z, m->r, m->d, m->S, m->sw.partials, c->st, nl), "cg direction");
+    }
   }
   if (rep) {
     rep->cg_iters += c->Sh->iters;
@@ -249,9 +257,12 @@ rve_status solve_step_impl(rve_ctx* c, const double dE[6], const void* init, rve
   while (!converged && rp->nr_iters < c->opts.max_nr) {
     rp->nr_iters++;
     if ((s = steihaug<R>(c, rp)) != RVE_OK) return s;
-    CK(trial_eval<R>(g, m->mt, m->phase, m->eps, m->z, m->khist, m->sig, m->D, m->sig_t, m->D_t, m->kap_t, m->S,
-                     m->sw.partials, c->st, nl),
-       "trial stress");
+    {
+      PassScope ps(&c->timer, c->st, PASS_TRIAL);
+      CK(trial_eval<R>(g, m->mt, m->phase, m->eps, m->z, m->khist, m->sig, m->D, m->sig_t, m->D_t, m->kap_t, m->S,
+                       m->sw.partials, c->st, nl),
+         "trial stress");
+    }
     CK(tr_decide(m->S, c->st, nl), "ratio test");
     if ((s = read_scalars<R>(c)) != RVE_OK) return s;
     if (c->Sh->nonfinite) return fail(c, RVE_ERR_NONFINITE, "non-finite trial state");
@@ -483,6 +494,27 @@ rve_status rve_solve_step(rve_t c, const double dE[6], const uint8_t fm[6], cons
   return DISPATCH(c, solve_step_impl, dE, init, rep);
 }
 
+rve_status rve_pass_timing(rve_t c, int enable) {
+  if (!c) return RVE_ERR_ARG;
+  if (!enable) {
+    c->timer.on = false;
+    return RVE_OK;
+  }
+  CK(c->timer.enable(16384), "timer events");
+  return RVE_OK;
+}
+
+rve_status rve_pass_stats(rve_t c, long long* counts, double* ms, int n) {
+  if (!c) return RVE_ERR_ARG;
+  if (!counts || !ms || n < 0) return fail(c, RVE_ERR_ARG, "NULL output");
+  CK(c->timer.flush(), "timer flush");
+  for (int i = 0; i < n; ++i) {
+    counts[i] = i < PASS_COUNT ? c->timer.counts[i] : 0;
+    ms[i] = i < PASS_COUNT ? c->timer.ms[i] : 0.0;
+  }
+  return RVE_OK;
+}
+
 const char* rve_last_error(rve_t c) { return c ? c->err.c_str() : g_create_error.c_str(); }
 
 long long rve_hv_count(rve_t c) { return c ? c->hv : 0; }
@@ -495,6 +527,7 @@ void rve_destroy(rve_t c) {
     else impl_free(impl_of<double>(c));
   }
   if (c->Sh) cudaFreeHost(c->Sh);
+  c->timer.destroy();
   delete c;
 }
 

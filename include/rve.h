@@ -171,6 +171,30 @@ rve_status rve_solve_step(rve_t, const double dE_host[6], const uint8_t free_mas
 rve_status rve_pass_timing(rve_t, int enable);
 rve_status rve_pass_stats(rve_t, long long* counts_host, double* ms_host, int n);
 
+/* Projection out = G : v (as rve_project, FP32 fields) for callers that must
+ * not allocate device memory: code past a fixed-budget initialisation phase
+ * (real-time or embedded loops, frameworks whose caching allocator owns all
+ * device memory) and code that must not trigger the implicit device-wide
+ * synchronisation cudaMalloc / cudaFree can cause.  The paper has no
+ * counterpart: this is a deployment variant of the projection.
+ *  dims, ndim     grid as for rve_create; limit: ncomp*Ny*Nz*(Nx/2+1) <=
+ *                 2087936 complex values (e.g. 80^3 in 3D, 1024^2 in 2D).
+ *  v_dev, out_dev ncomp x Nvox FP32 device fields (may alias), caller-owned.
+ *  free_mask_host stress-controlled mean components (NULL = none).
+ *  stream         cudaStream_t (as void*); NULL = legacy default stream.
+ * No context is needed and nothing is allocated: the scratch (axis tables
+ * and half spectrum) lives in a fixed 16 MiB __device__ array that every GPU
+ * loading the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.
+ * Every call on a device shares the array and overwrites it (nothing in it
+ * needs to start at zero); calls whose work overlaps on the GPU (different
+ * streams, or host threads without ordering) race on it and must be
+ * serialised by the caller.  Returns RVE_ERR_ARG (NULL pointer, bad dims,
+ * grid over the limit) or RVE_ERR_CUDA; no message is stored. */
+rve_status rve_project_noalloc(const int dims[3], int ndim, const float* v_dev, float* out_dev,
+                               const uint8_t free_mask_host[6], void* stream);
+
 /* Message of the last error on this context (static storage; never NULL). */
 const char* rve_last_error(rve_t);
 

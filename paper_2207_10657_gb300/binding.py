@@ -63,6 +63,8 @@ _SIGS = [
     ("rve_pass_timing", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("rve_pass_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    ("rve_project_noalloc", ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint8), ctypes.c_void_p]),
     ("rve_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("rve_hv_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("rve_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
@@ -173,6 +175,17 @@ def rve_pass_stats(h):
     ms = (ctypes.c_double * n)()
     check(lib().rve_pass_stats(h, counts, ms, n), h)
     return {PASS_NAMES[i]: (counts[i], ms[i]) for i in range(n)}
+
+
+def rve_project_noalloc(dims, v_ptr, out_ptr, free_mask=None, stream=0):
+    """Projection with no device allocation (scratch in a fixed 16 MiB
+    device array inside the library); returns the status code."""
+    d = (ctypes.c_int * 3)(*(list(dims) + [1] * (3 - len(dims))))
+    fm = None
+    if free_mask is not None:
+        fm = (ctypes.c_uint8 * 6)(*[1 if x else 0 for x in (list(free_mask) + [0] * (6 - len(free_mask)))])
+    return lib().rve_project_noalloc(d, len(dims), ctypes.c_void_p(v_ptr), ctypes.c_void_p(out_ptr), fm,
+                                     ctypes.c_void_p(stream))
 
 
 def rve_last_error(h):

@@ -361,6 +361,37 @@ cudaError_t spectral_setup(const GridDesc& g, SpecWork<R>& w) {
   return cudaGetLastError();
 }
 
+// Plans and tile sizes for a caller that brings its own tables and spectrum
+// storage (no device allocation): the same choices as spectral_setup.
+template <typename R>
+cudaError_t spectral_plan(const GridDesc& g, SpecWork<R>& w) {
+  using C = Cx<R>;
+  make_plan(g.nx, w.px);
+  make_plan(g.ny, w.py);
+  make_plan(g.ndim == 3 ? g.nz : 1, w.pz);
+  const int ex = kXThreads * kXEpt;
+  int q = (2 * ex) / (g.ncomp * g.nx);
+  if (g.ncomp & 1) q &= ~1;
+  q = std::max(q, (g.ncomp & 1) ? 2 : 1);
+  w.qx = (int)std::min<long long>(q, g.nrows + (g.nrows & 1));
+  const int ey = kYThreads * kYEpt;
+  w.ty = std::max(1, std::min(pow2_floor(std::max(1, ey / g.ny)), 64));
+  if (g.ndim == 3) {
+    const int ez = std::min(kZThreads * kZEpt, (int)(kSmemCap / sizeof(C)));
+    w.tz = std::max(1, std::min(pow2_floor(std::max(1, ez / (6 * g.nz))), 16));
+  } else {
+    const int e2 = std::min(kYThreads * kYEpt, (int)(kSmemCap / sizeof(C)));
+    w.tz = std::max(1, std::min(pow2_floor(std::max(1, e2 / (3 * g.ny))), 64));
+  }
+  cudaFuncSetAttribute(k_xfwd<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_ycols<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_ycols<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_zproj<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_yproj2d<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  cudaFuncSetAttribute(k_xinv<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
+  return cudaGetLastError();
+}
+
 template <typename R>
 void spectral_free(SpecWork<R>& w) {
   for (int a = 0; a < 3; ++a) {
@@ -476,6 +507,7 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
 
 template cudaError_t spectral_setup<float>(const GridDesc&, SpecWork<float>&);
 template cudaError_t spectral_setup<double>(const GridDesc&, SpecWork<double>&);
+template cudaError_t spectral_plan<float>(const GridDesc&, SpecWork<float>&);
 template void spectral_free<float>(SpecWork<float>&);
 template void spectral_free<double>(SpecWork<double>&);
 template cudaError_t spectral_apply<float>(const GridDesc&, SpecWork<float>&, const MatTable<float>&, const float*,

@@ -45,6 +45,10 @@ template <typename R>
 cudaError_t spectral_setup(const GridDesc& g, SpecWork<R>& w);
 template <typename R>
 void spectral_free(SpecWork<R>& w);
+// Plans and tile sizes only, no device allocation (the caller provides
+// the tables and the spectrum storage in SpecWork).
+template <typename R>
+cudaError_t spectral_plan(const GridDesc& g, SpecWork<R>& w);
 
 // FP64 final reduction of per-block partials: out[s] = sum_b part[b*ns + s]
 // (out: ns contiguous device doubles).  Fixed summation order.

@@ -1,8 +1,10 @@
 // FP32 spectral passes specialised at compile time for the common axis
 // lengths (powers of two from 32 to 512 and 3 * 2^k up to 384).  Same data
 // layout and the same arithmetic as the generic passes in hv_passes.cu;
-// only the FFT engine (fft_fast.cuh) and the global I/O (float4 rows)
-// differ.
+// only the FFT engine (fft_fast.cuh) and the staging differ: global loads
+// are batched in registers before they are written to shared memory, and
+// the x passes give consecutive threads consecutive x so that the
+// line-interleaved shared-memory accesses stay (nearly) conflict free.
 #include "fft_fast.cuh"
 #include "hv_passes.cuh"
 #include "hv_fast.cuh"
@@ -23,8 +25,9 @@ template <int N, int NC> constexpr int xq() {
   return ((nl & 1) == 0 && q2 > ((NC & 1) ? 2 : 1)) ? q2 - ((NC & 1) ? 2 : 1) : q2;
 }
 template <int N> constexpr int ytx() { return (kFBudget / N) < 16 ? (kFBudget / N) : 16; }
-template <int N> constexpr int ztx() { return N <= 256 ? (N <= 64 ? 16 : 8) : 4; }
-template <int N> constexpr int zthreads() { return N >= 256 ? 512 : 256; }
+template <int N> constexpr int ztx() { return N <= 64 ? 16 : 4; }
+template <int N> constexpr int zthreads() { return N >= 512 ? 512 : 256; }
+template <int N> constexpr int zminblocks() { return N >= 512 ? 1 : 3; }
 template <int N> constexpr int p2tx() { return (kFBudget / (3 * N)) < 16 ? (kFBudget / (3 * N)) : 16; }
 
 // ------------------------------------------------------------ x forward
@@ -36,46 +39,46 @@ __global__ void __launch_bounds__(kFT)
   constexpr int Q = xq<N, NC>();
   constexpr int NL = NC * Q / 2;
   constexpr int ND = NC == 6 ? 3 : 2;
-  constexpr int N4 = N / 4;
   __shared__ __align__(16) float2 buf[NL * N];
   const long long row0 = (long long)blockIdx.x * Q;
-  for (int idx = threadIdx.x; idx < Q * N4; idx += kFT) {
-    const int q = idx / N4, x4 = idx - (idx / N4) * N4;
-    const long long row = row0 + q;
-    float4 v[NC];
+  // one voxel per thread per step: consecutive threads take consecutive x,
+  // so the line-interleaved shared-memory writes are (nearly) conflict free
+  constexpr int ITEMS = Q * N;
+  constexpr int STEPS = (ITEMS + kFT - 1) / kFT;
+  constexpr int BATCH = STEPS < 4 ? STEPS : 4;
+  for (int s0 = 0; s0 < STEPS; s0 += BATCH) {
+    float v[BATCH][NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) v[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (row < nrows) {
-      const long long vox = row * N + 4 * x4;
+    for (int b = 0; b < BATCH; ++b) {
+      const int idx = threadIdx.x + (s0 + b) * kFT;
+      const int q = idx / N, x = idx - (idx / N) * N;
+      const long long row = row0 + q;
+      const bool ok = (s0 + b < STEPS) && idx < ITEMS && row < nrows;
+      const long long vox = row * N + x;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) v[c] = __ldg(reinterpret_cast<const float4*>(in + c * nvox + vox));
-      if (MODE == 1) {
-        const float4 d4 = __ldg(reinterpret_cast<const float4*>(dmg + vox));
-        const uchar4 p4 = __ldg(reinterpret_cast<const uchar4*>(phase + vox));
-        const float dd[4] = {d4.x, d4.y, d4.z, d4.w};
-        const int pp[4] = {p4.x, p4.y, p4.z, p4.w};
+      for (int c = 0; c < NC; ++c) v[b][c] = ok ? __ldg(in + c * nvox + vox) : 0.f;
+      if (MODE == 1 && ok) {
+        const float keep = 1.f - __ldg(dmg + vox);
+        const int ph = __ldg(phase + vox);
+        const float lam = mt.lam[ph] * keep, tmu = 2.f * mt.mu[ph] * keep;
+        float tr = 0.f;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float keep = 1.f - dd[e];
-          const float lam = mt.lam[pp[e]] * keep, tmu = 2.f * mt.mu[pp[e]] * keep;
-          float* f[NC];
+        for (int i = 0; i < ND; ++i) tr += v[b][i];
 #pragma unroll
-          for (int c = 0; c < NC; ++c) f[c] = reinterpret_cast<float*>(&v[c]) + e;
-          float tr = 0.f;
-#pragma unroll
-          for (int i = 0; i < ND; ++i) tr += *f[i];
-#pragma unroll
-          for (int c = 0; c < NC; ++c) *f[c] = tmu * *f[c] + (c < ND ? lam * tr : 0.f);
-        }
+        for (int c = 0; c < NC; ++c) v[b][c] = tmu * v[b][c] + (c < ND ? lam * tr : 0.f);
       }
     }
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const int rho = q * NC + c;
-      const int p = rho >> 1, h = rho & 1;
-      const float* ve = reinterpret_cast<const float*>(&v[c]);
+    for (int b = 0; b < BATCH; ++b) {
+      const int idx = threadIdx.x + (s0 + b) * kFT;
+      if (s0 + b < STEPS && idx < ITEMS) {
+        const int q = idx / N, x = idx - (idx / N) * N;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) reinterpret_cast<float*>(&buf[(4 * x4 + e) * NL + p])[h] = ve[e];
+        for (int c = 0; c < NC; ++c) {
+          const int rho = q * NC + c;
+          reinterpret_cast<float*>(&buf[x * NL + (rho >> 1)])[rho & 1] = v[b][c];
+        }
+      }
     }
   }
   __syncthreads();
@@ -105,57 +108,71 @@ __global__ void __launch_bounds__(kFT)
             const float2* __restrict__ tw, const float scale, const bool self_dot) {
   constexpr int Q = xq<N, NC>();
   constexpr int NL = NC * Q / 2;
-  constexpr int N4 = N / 4;
   constexpr int NXH = N / 2 + 1;
   constexpr int HALF = N / 2;
   __shared__ __align__(16) float2 buf[NL * N];
   __shared__ double red[32];
   const long long row0 = (long long)blockIdx.x * Q;
-  for (int idx = threadIdx.x; idx < NL * N; idx += kFT) {
-    const int p = idx / N, k = idx - (idx / N) * N;
-    float2 xh[2];
+  constexpr int LITEMS = NL * N;
+  constexpr int LSTEPS = (LITEMS + kFT - 1) / kFT;
+  constexpr int LB = LSTEPS < 4 ? LSTEPS : 4;
+  for (int s0 = 0; s0 < LSTEPS; s0 += LB) {
+    float2 xh[LB][2];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int rho = 2 * p + h;
-      const int q = rho / NC, c = rho - (rho / NC) * NC;
-      const long long row = row0 + q;
-      float2 x = make_float2(0.f, 0.f);
-      if (row < nrows) {
-        const int kk = k <= HALF ? k : N - k;
-        x = spec[(c * nrows + row) * NXH + kk];
-        if (kk == 0 || kk == HALF) x.y = 0.f;
-        if (k > HALF) x.y = -x.y;
+    for (int b = 0; b < LB; ++b) {
+      const int idx = threadIdx.x + (s0 + b) * kFT;
+      const int p = idx / N, k = idx - (idx / N) * N;
+      const int kk = k <= HALF ? k : N - k;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int rho = 2 * p + h;
+        const int q = rho / NC, c = rho - (rho / NC) * NC;
+        const long long row = row0 + q;
+        xh[b][h] = (s0 + b < LSTEPS && idx < LITEMS && row < nrows) ? spec[(c * nrows + row) * NXH + kk]
+                                                                   : make_float2(0.f, 0.f);
       }
-      xh[h] = x;
     }
-    buf[k * NL + p] = make_float2(xh[0].x - xh[1].y, xh[0].y + xh[1].x);
+#pragma unroll
+    for (int b = 0; b < LB; ++b) {
+      const int idx = threadIdx.x + (s0 + b) * kFT;
+      if (s0 + b < LSTEPS && idx < LITEMS) {
+        const int p = idx / N, k = idx - (idx / N) * N;
+        const int kk = k <= HALF ? k : N - k;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (kk == 0 || kk == HALF) xh[b][h].y = 0.f;
+          if (k > HALF) xh[b][h].y = -xh[b][h].y;
+        }
+        buf[k * NL + p] = make_float2(xh[b][0].x - xh[b][1].y, xh[b][0].y + xh[b][1].x);
+      }
+    }
   }
   __syncthreads();
   fft_ct<N, NL, kFT, true>(buf, tw);
   KSum<float> acc;
-  for (int idx = threadIdx.x; idx < Q * NC * N4; idx += kFT) {
-    const int rho = idx / N4, x4 = idx - (idx / N4) * N4;
-    const int q = rho / NC, c = rho - (rho / NC) * NC;
-    const long long row = row0 + q;
-    if (row < nrows) {
-      const int p = rho >> 1, h = rho & 1;
-      float4 o;
-      float* oe = reinterpret_cast<float*>(&o);
+  constexpr int SITEMS = Q * NC * N;
+  constexpr int SSTEPS = (SITEMS + kFT - 1) / kFT;
+  constexpr int SB = SSTEPS < 8 ? SSTEPS : 8;
+  for (int s0 = 0; s0 < SSTEPS; s0 += SB) {
+    float o[SB], w[SB];
+    long long off[SB];
+    bool ok[SB];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) oe[e] = reinterpret_cast<const float*>(&buf[(4 * x4 + e) * NL + p])[h] * scale;
-      const long long off = c * nvox + row * N + 4 * x4;
-      *reinterpret_cast<float4*>(out + off) = o;
-      if (DOT) {
-        if (self_dot) {
+    for (int b = 0; b < SB; ++b) {
+      const int idx = threadIdx.x + (s0 + b) * kFT;
+      const int rho = idx / N, x = idx - (idx / N) * N;
+      const int q = rho / NC, c = rho - (rho / NC) * NC;
+      const long long row = row0 + q;
+      ok[b] = (s0 + b < SSTEPS) && idx < SITEMS && row < nrows;
+      off[b] = c * nvox + row * N + x;
+      o[b] = ok[b] ? reinterpret_cast<const float*>(&buf[x * NL + (rho >> 1)])[rho & 1] * scale : 0.f;
+      w[b] = (DOT && ok[b]) ? (self_dot ? o[b] : __ldg(dotw + off[b])) : 0.f;
+    }
 #pragma unroll
-          for (int e = 0; e < 4; ++e) acc.add(oe[e] * oe[e]);
-        } else {
-          const float4 w = __ldg(reinterpret_cast<const float4*>(dotw + off));
-          acc.add(o.x * w.x);
-          acc.add(o.y * w.y);
-          acc.add(o.z * w.z);
-          acc.add(o.w * w.w);
-        }
+    for (int b = 0; b < SB; ++b) {
+      if (ok[b]) {
+        out[off[b]] = o[b];
+        if (DOT) acc.add(o[b] * w[b]);
       }
     }
   }
@@ -175,9 +192,18 @@ __global__ void __launch_bounds__(kFT)
   const int kx0 = blockIdx.x * TX;
   const int tv = min(TX, nxh - kx0);
   const long long plane = ((long long)blockIdx.z * nz + blockIdx.y) * N;
-  for (int idx = threadIdx.x; idx < N * TX; idx += kFT) {
+  constexpr int STEPS = (N * TX + kFT - 1) / kFT;
+  float2 tmp[STEPS];
+#pragma unroll
+  for (int i = 0; i < STEPS; ++i) {
+    const int idx = threadIdx.x + i * kFT;
     const int y = idx / TX, t = idx - (idx / TX) * TX;
-    buf[idx] = t < tv ? spec[(plane + y) * nxh + kx0 + t] : make_float2(0.f, 0.f);
+    tmp[i] = (idx < N * TX && t < tv) ? spec[(plane + y) * nxh + kx0 + t] : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < STEPS; ++i) {
+    const int idx = threadIdx.x + i * kFT;
+    if (idx < N * TX) buf[idx] = tmp[i];
   }
   __syncthreads();
   fft_ct<N, TX, kFT, INV>(buf, tw);
@@ -189,7 +215,7 @@ __global__ void __launch_bounds__(kFT)
 
 // ------------------------------------------------- z + projection (3D)
 template <int N>
-__global__ void __launch_bounds__(zthreads<N>())
+__global__ void __launch_bounds__(zthreads<N>(), zminblocks<N>())
     kf_zproj(float2* __restrict__ spec, const int ny, const int nxh, const float2* __restrict__ tw,
              const float2* __restrict__ gdx, const float2* __restrict__ gax, const float2* __restrict__ gdy,
              const float2* __restrict__ gay, const float2* __restrict__ gdz, const float2* __restrict__ gaz,
@@ -201,10 +227,24 @@ __global__ void __launch_bounds__(zthreads<N>())
   float2* buf = reinterpret_cast<float2*>(smem_raw);
   const int kx0 = blockIdx.x * TX, ky = blockIdx.y;
   const int tv = min(TX, nxh - kx0);
-  for (int idx = threadIdx.x; idx < N * NL; idx += NT) {
-    const int z = idx / NL, rem = idx - (idx / NL) * NL;
-    const int c = rem / TX, t = rem - (rem / TX) * TX;
-    buf[idx] = t < tv ? spec[(((long long)c * N + z) * ny + ky) * nxh + kx0 + t] : make_float2(0.f, 0.f);
+  constexpr int STEPS = (N * NL + NT - 1) / NT;
+  constexpr int LB = STEPS < 8 ? STEPS : 8;
+  for (int s0 = 0; s0 < STEPS; s0 += LB) {
+    float2 tmp[LB];
+#pragma unroll
+    for (int b = 0; b < LB; ++b) {
+      const int idx = threadIdx.x + (s0 + b) * NT;
+      const int z = idx / NL, rem = idx - (idx / NL) * NL;
+      const int c = rem / TX, t = rem - (rem / TX) * TX;
+      tmp[b] = (s0 + b < STEPS && idx < N * NL && t < tv)
+                   ? spec[(((long long)c * N + z) * ny + ky) * nxh + kx0 + t]
+                   : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int b = 0; b < LB; ++b) {
+      const int idx = threadIdx.x + (s0 + b) * NT;
+      if (s0 + b < STEPS && idx < N * NL) buf[idx] = tmp[b];
+    }
   }
   __syncthreads();
   fft_ct<N, NL, NT, false>(buf, tw);

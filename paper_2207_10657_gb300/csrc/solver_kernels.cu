@@ -85,17 +85,39 @@ __device__ __forceinline__ R damage_of(R k, R k0, R kf) {
 }
 
 // ------------------------------------------------------------ CG kernels
+// Vector kernels stream 4-wide vectors (n is a multiple of 4: every grid
+// dimension is even), two per thread per iteration, to keep enough bytes
+// in flight per SM.
+template <typename R> struct V4T;
+template <> struct V4T<float> { using T = float4; };
+template <> struct V4T<double> { using T = double4; };
+template <typename R> using V4 = typename V4T<R>::T;
+template <typename R> __device__ __forceinline__ R& el(V4<R>& v, int i) { return (&v.x)[i]; }
+template <typename R> __device__ __forceinline__ R elc(const V4<R>& v, int i) { return (&v.x)[i]; }
+template <typename R> __device__ __forceinline__ V4<R> ld4(const R* p, long long i) {
+  return *reinterpret_cast<const V4<R>*>(p + 4 * i);
+}
+template <typename R> __device__ __forceinline__ void st4(R* p, long long i, const V4<R>& v) {
+  *reinterpret_cast<V4<R>*>(p + 4 * i) = v;
+}
 template <typename R>
 __global__ void __launch_bounds__(kVThreads)
     k_cg_init(long long n, const R* __restrict__ g, R* __restrict__ z, R* __restrict__ r, R* __restrict__ d,
               double* __restrict__ part) {
   KSum<R> acc[1];
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const R gi = g[i];
-    z[i] = 0;
-    r[i] = gi;
-    d[i] = -gi;
-    acc[0].add(gi * gi);
+  const long long n4 = n / 4;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+    const V4<R> gi = ld4(g, i);
+    V4<R> zero, neg;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      el<R>(zero, e) = 0;
+      el<R>(neg, e) = -elc<R>(gi, e);
+      acc[0].add(elc<R>(gi, e) * elc<R>(gi, e));
+    }
+    st4(z, i, zero);
+    st4(r, i, gi);
+    st4(d, i, neg);
   }
   finish_sums<R, 1>(acc, part);
 }
@@ -148,21 +170,51 @@ __global__ void __launch_bounds__(kVThreads)
                 const R* __restrict__ Hd, const DevScalars* __restrict__ S, double* __restrict__ part) {
   const int status = S->status;
   KSum<R> acc[3];
+  const long long n4 = n / 4;
+  const long long stride = (long long)gridDim.x * blockDim.x;
   if (status == CG_BOUNDARY || status == CG_NEGCURV) {
     const R tau = (R)S->tau;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-      z[i] += tau * d[i];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+      V4<R> zi = ld4(z, i);
+      const V4<R> di = ld4(d, i);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) el<R>(zi, e) += tau * elc<R>(di, e);
+      st4(z, i, zi);
+    }
   } else if (status == CG_RUN) {
     const R a = (R)S->alpha;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-      const R zi = z[i] + a * d[i];
-      const R ro = r[i];
-      const R rn = ro + a * Hd[i];
-      z[i] = zi;
-      r[i] = rn;
-      acc[0].add(rn * rn);
-      acc[1].add(rn * ro);
-      acc[2].add(zi * zi);
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i < n4; i += 2 * stride) {
+      V4<R> zi[2], ro[2], di[2], hi[2];
+      const bool two = i + stride < n4;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (u == 0 || two) {
+          zi[u] = ld4(z, i + u * stride);
+          ro[u] = ld4(r, i + u * stride);
+          di[u] = ld4(d, i + u * stride);
+          hi[u] = ld4(Hd, i + u * stride);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (u == 0 || two) {
+          V4<R> zn, rn;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const R zz = el<R>(zi[u], e) + a * el<R>(di[u], e);
+            const R ov = el<R>(ro[u], e);
+            const R nv = ov + a * el<R>(hi[u], e);
+            el<R>(zn, e) = zz;
+            el<R>(rn, e) = nv;
+            acc[0].add(nv * nv);
+            acc[1].add(nv * ov);
+            acc[2].add(zz * zz);
+          }
+          st4(z, i + u * stride, zn);
+          st4(r, i + u * stride, rn);
+        }
+      }
     }
   }
   finish_sums<R, 3>(acc, part);
@@ -189,10 +241,16 @@ __global__ void __launch_bounds__(kVThreads)
     k_cg_restart(long long n, R* __restrict__ r, const R* __restrict__ Hz, const R* __restrict__ g,
                  double* __restrict__ part) {
   KSum<R> acc[1];
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const R ri = Hz[i] + g[i];
-    r[i] = ri;
-    acc[0].add(ri * ri);
+  const long long n4 = n / 4;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+    const V4<R> h = ld4(Hz, i), gg = ld4(g, i);
+    V4<R> ri;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      el<R>(ri, e) = elc<R>(h, e) + elc<R>(gg, e);
+      acc[0].add(el<R>(ri, e) * el<R>(ri, e));
+    }
+    st4(r, i, ri);
   }
   finish_sums<R, 1>(acc, part);
 }
@@ -210,13 +268,35 @@ __global__ void __launch_bounds__(kVThreads)
                  const DevScalars* __restrict__ S, double* __restrict__ part) {
   const R beta = (R)S->beta;
   KSum<R> acc[3];
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const R ri = r[i];
-    const R di = -ri + beta * d[i];
-    d[i] = di;
-    acc[0].add(di * di);
-    acc[1].add(z[i] * di);
-    acc[2].add(ri * di);
+  const long long n4 = n / 4;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += 2 * stride) {
+    V4<R> zi[2], ri[2], di[2];
+    const bool two = i + stride < n4;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (u == 0 || two) {
+        zi[u] = ld4(z, i + u * stride);
+        ri[u] = ld4(r, i + u * stride);
+        di[u] = ld4(d, i + u * stride);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (u == 0 || two) {
+        V4<R> dn;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const R rv = el<R>(ri[u], e);
+          const R dv = -rv + beta * el<R>(di[u], e);
+          el<R>(dn, e) = dv;
+          acc[0].add(dv * dv);
+          acc[1].add(el<R>(zi[u], e) * dv);
+          acc[2].add(rv * dv);
+        }
+        st4(d, i + u * stride, dn);
+      }
+    }
   }
   finish_sums<R, 3>(acc, part);
 }
@@ -225,49 +305,72 @@ __global__ void __launch_bounds__(kVThreads)
 // sigma_t = (1 - D_t) C : (eps + p), kappa_t = max(kappa_n, kappa(eps + p))
 // on damaging phases.  Sums (group T): sig0:p, sig_t:p, p:(1-D0)C:p,
 // sig_t:sig_t, p:p, (eps+p):(eps+p).
-template <typename R>
+template <typename R, int NC>
 __global__ void __launch_bounds__(kVThreads)
     k_trial(const GridDesc g, const MatTable<R> mt, const uint8_t* __restrict__ phase, const R* __restrict__ eps,
             const R* __restrict__ p, const R* __restrict__ khist, const R* __restrict__ sig0,
             const R* __restrict__ D0, R* __restrict__ sig_t, R* __restrict__ D_t, R* __restrict__ kap_t,
             double* __restrict__ part) {
-  const int nc = g.ncomp, nd = g.ndim;
-  const long long nv = g.nvox;
+  // four consecutive voxels per thread (nvox is a multiple of 4)
+  constexpr int nc = NC, nd = NC == 6 ? 3 : 2;
+  const long long nv = g.nvox, nv4 = nv / 4;
   KSum<R> acc[6];
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
-    R e[6], pv[6];
+  for (long long v4 = (long long)blockIdx.x * blockDim.x + threadIdx.x; v4 < nv4;
+       v4 += (long long)gridDim.x * blockDim.x) {
+    V4<R> e[6], pv[6], s0[6];
+#pragma unroll
     for (int c = 0; c < nc; ++c) {
-      pv[c] = p ? p[c * nv + v] : (R)0;
-      e[c] = eps[c * nv + v] + pv[c];
+      e[c] = ld4(eps + c * nv, v4);
+      if (p) pv[c] = ld4(p + c * nv, v4);
+      else pv[c] = V4<R>{0, 0, 0, 0};
+      if (sig0) s0[c] = ld4(sig0 + c * nv, v4);
     }
-    const int ph = phase[v];
-    const R lam = mt.lam[ph], mu = mt.mu[ph];
-    R D = 0;
-    R kap = 0;
-    if (mt.damaging[ph]) {
-      const R kt = kappa_tension<R>(e, nd);
-      const R kh = khist ? khist[v] : (R)0;
-      const R k = fmax(kh, kt);
-      kap = k;
-      D = damage_of<R>(k, mt.kappa0[ph], mt.kappaf[ph]);
+    const V4<R> kh4 = khist ? ld4(khist, v4) : V4<R>{0, 0, 0, 0};
+    const V4<R> d04 = D0 ? ld4(D0, v4) : V4<R>{0, 0, 0, 0};
+    const uchar4 ph4 = *reinterpret_cast<const uchar4*>(phase + 4 * v4);
+    const int phs[4] = {ph4.x, ph4.y, ph4.z, ph4.w};
+    V4<R> sg[6], Dq, kq;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      R ev[6], pq[6];
+#pragma unroll
+      for (int c = 0; c < nc; ++c) {
+        pq[c] = elc<R>(pv[c], q);
+        ev[c] = elc<R>(e[c], q) + pq[c];
+      }
+      const int ph = phs[q];
+      const R lam = mt.lam[ph], mu = mt.mu[ph];
+      R D = 0, kap = 0;
+      if (mt.damaging[ph]) {
+        const R kt = kappa_tension<R>(ev, nd);
+        const R k = fmax(elc<R>(kh4, q), kt);
+        kap = k;
+        D = damage_of<R>(k, mt.kappa0[ph], mt.kappaf[ph]);
+      }
+      const R keep = (R)1 - D;
+      R tr = 0, trp = 0;
+#pragma unroll
+      for (int i = 0; i < nd; ++i) { tr += ev[i]; trp += pq[i]; }
+      const R keep0 = (R)1 - elc<R>(d04, q);
+#pragma unroll
+      for (int c = 0; c < nc; ++c) {
+        const R sv = keep * ((R)2 * mu * ev[c] + (c < nd ? lam * tr : (R)0));
+        el<R>(sg[c], q) = sv;
+        const R bp = keep0 * ((R)2 * mu * pq[c] + (c < nd ? lam * trp : (R)0));
+        if (sig0) acc[0].add(elc<R>(s0[c], q) * pq[c]);
+        acc[1].add(sv * pq[c]);
+        acc[2].add(pq[c] * bp);
+        acc[3].add(sv * sv);
+        acc[4].add(pq[c] * pq[c]);
+        acc[5].add(ev[c] * ev[c]);
+      }
+      el<R>(Dq, q) = D;
+      el<R>(kq, q) = kap;
     }
-    const R keep = (R)1 - D;
-    R tr = 0, trp = 0;
-    for (int i = 0; i < nd; ++i) { tr += e[i]; trp += pv[i]; }
-    const R keep0 = D0 ? (R)1 - D0[v] : (R)1;
-    for (int c = 0; c < nc; ++c) {
-      const R s = keep * ((R)2 * mu * e[c] + (c < nd ? lam * tr : (R)0));
-      sig_t[c * nv + v] = s;
-      const R bp = keep0 * ((R)2 * mu * pv[c] + (c < nd ? lam * trp : (R)0));
-      if (sig0) acc[0].add(sig0[c * nv + v] * pv[c]);
-      acc[1].add(s * pv[c]);
-      acc[2].add(pv[c] * bp);
-      acc[3].add(s * s);
-      acc[4].add(pv[c] * pv[c]);
-      acc[5].add(e[c] * e[c]);
-    }
-    if (D_t) D_t[v] = D;
-    if (kap_t) kap_t[v] = kap;
+#pragma unroll
+    for (int c = 0; c < nc; ++c) st4(sig_t + c * nv, v4, sg[c]);
+    if (D_t) st4(D_t, v4, Dq);
+    if (kap_t) st4(kap_t, v4, kq);
   }
   finish_sums<R, 6>(acc, part);
 }
@@ -292,8 +395,14 @@ __global__ void k_tr_decide(DevScalars* S) {
 
 template <typename R>
 __global__ void __launch_bounds__(kVThreads) k_axpy(long long n, R a, const R* __restrict__ x, R* __restrict__ y) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] += a * x[i];
+  const long long n4 = n / 4;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+    const V4<R> xi = ld4(x, i);
+    V4<R> yi = ld4(y, i);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) el<R>(yi, e) += a * elc<R>(xi, e);
+    st4(y, i, yi);
+  }
 }
 
 struct Inc6 { double v[6]; };
@@ -385,7 +494,10 @@ template <typename R>
 cudaError_t trial_eval(const GridDesc& g, const MatTable<R>& mt, const uint8_t* phase, const R* eps, const R* p,
                        const R* khist, const R* sig0, const R* D0, R* sig_t, R* D_t, R* kap_t,
                        DevScalars* S, double* part, cudaStream_t st, long long* nl) {
-  k_trial<R><<<kVBlocks, kVThreads, 0, st>>>(g, mt, phase, eps, p, khist, sig0, D0, sig_t, D_t, kap_t, part);
+  if (g.ncomp == 6)
+    k_trial<R, 6><<<kVBlocks, kVThreads, 0, st>>>(g, mt, phase, eps, p, khist, sig0, D0, sig_t, D_t, kap_t, part);
+  else
+    k_trial<R, 3><<<kVBlocks, kVThreads, 0, st>>>(g, mt, phase, eps, p, khist, sig0, D0, sig_t, D_t, kap_t, part);
   RVE_TRY(cudaGetLastError());
   *nl += 1;
   return reduce_partials(part, kVBlocks, 6, &S->sp, st, nl);

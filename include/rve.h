@@ -195,6 +195,46 @@ rve_status rve_pass_stats(rve_t, long long* counts_host, double* ms_host, int n)
 rve_status rve_project_noalloc(const int dims[3], int ndim, const float* v_dev, float* out_dev,
                                const uint8_t free_mask_host[6], void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batched solver: n RVEs of uneven sizes (2D and 3D may be mixed) advanced
+ * in lockstep, FP32 fields.  Each step of the path (tangent + FFT passes +
+ * projection, CG reductions and updates, constitutive update, scalar
+ * control) is one persistent launch over all members, pulling (member,
+ * block) work items from a counter; the inner CG iteration is replayed from
+ * a captured CUDA graph.  Same method and results as n independent contexts.
+ * ------------------------------------------------------------------------ */
+typedef struct rve_batch_ctx* rve_batch_t;
+
+/* dims: n*3 ints (Nx, Ny, Nz per member; Nz ignored in 2D); ndims: n ints;
+ * phase_ids_dev: host array of n device pointers (Nvox_i uint8 each, copied);
+ * phases shared by all members; opts as for rve_create (precision 32 only).
+ * 1 <= n <= 256. */
+rve_status rve_batch_create(int n, const int* dims_host, const int* ndims_host,
+                            const uint8_t* const* phase_ids_dev, const rve_phase* phases_host,
+                            int nphase, const rve_solver_opts* opts_host, void* stream,
+                            rve_batch_t* out);
+/* One load step of Algorithm 2 for every member: dE_host n*6 (Mandel, per
+ * member), free_mask_host n*6 or NULL (keep), reps_host n reports.
+ * Returns RVE_ERR_NOT_CONVERGED if any member hit max_nr (its history is
+ * not committed; converged members commit theirs). */
+rve_status rve_batch_solve_step(rve_batch_t, const double* dE_host, const uint8_t* free_mask_host,
+                                rve_step_report* reps_host);
+/* One batched Hessian-vector product out_i = G:((1-D_i)C:v_i) on every
+ * member (host arrays of n device pointers, ncomp*Nvox_i floats each). */
+rve_status rve_batch_hessp(rve_batch_t, const float* const* v_dev, float* const* out_dev);
+/* Frozen damage of member i (Nvox_i floats), as rve_set_damage. */
+rve_status rve_batch_set_damage(rve_batch_t, int i, const float* damage_dev);
+/* State of member i, as rve_get_state (any pointer may be NULL). */
+rve_status rve_batch_get_state(rve_batch_t, int i, float* strain_dev, float* kappa_dev,
+                               float* stress_dev, float* damage_dev);
+/* Back to the unloaded state (eps = 0, kappa_n = 0) for every member; the
+ * trust radii are kept. */
+rve_status rve_batch_reset(rve_batch_t);
+const char* rve_batch_last_error(rve_batch_t);
+long long rve_batch_hv_count(rve_batch_t);
+long long rve_batch_launch_count(rve_batch_t);
+void rve_batch_destroy(rve_batch_t);
+
 /* Message of the last error on this context (static storage; never NULL). */
 const char* rve_last_error(rve_t);
 

@@ -65,6 +65,22 @@ _SIGS = [
                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     ("rve_project_noalloc", ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint8), ctypes.c_void_p]),
+    ("rve_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(rve_phase), ctypes.c_int,
+                                        ctypes.POINTER(rve_solver_opts), ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    ("rve_batch_solve_step", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(rve_step_report)]),
+    ("rve_batch_hessp", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    ("rve_batch_set_damage", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("rve_batch_get_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
+    ("rve_batch_reset", ctypes.c_int, [ctypes.c_void_p]),
+    ("rve_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("rve_batch_hv_count", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("rve_batch_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("rve_batch_destroy", None, [ctypes.c_void_p]),
     ("rve_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("rve_hv_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("rve_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
@@ -186,6 +202,70 @@ def rve_project_noalloc(dims, v_ptr, out_ptr, free_mask=None, stream=0):
         fm = (ctypes.c_uint8 * 6)(*[1 if x else 0 for x in (list(free_mask) + [0] * (6 - len(free_mask)))])
     return lib().rve_project_noalloc(d, len(dims), ctypes.c_void_p(v_ptr), ctypes.c_void_p(out_ptr), fm,
                                      ctypes.c_void_p(stream))
+
+
+def _bcheck(status, handle):
+    if status != RVE_OK:
+        raise RveError(status, lib().rve_batch_last_error(handle).decode())
+
+
+def rve_batch_create(dims_list, phase_ptrs, phases, opts=None, stream=0):
+    n = len(dims_list)
+    dims = (ctypes.c_int * (3 * n))(*[x for d in dims_list for x in (list(d) + [1] * (3 - len(d)))])
+    nd = (ctypes.c_int * n)(*[len(d) for d in dims_list])
+    ptrs = (ctypes.c_void_p * n)(*phase_ptrs)
+    arr = (rve_phase * len(phases))(*[rve_phase(*p) for p in phases])
+    h = ctypes.c_void_p()
+    st = lib().rve_batch_create(n, dims, nd, ptrs, arr, len(phases),
+                                ctypes.byref(opts) if opts is not None else None, ctypes.c_void_p(stream),
+                                ctypes.byref(h))
+    _bcheck(st, None)
+    return h
+
+
+def rve_batch_solve_step(h, dE_list, free_masks=None, raise_on_error=True):
+    n = len(dE_list)
+    de = (ctypes.c_double * (6 * n))(*[x for d in dE_list for x in (list(d) + [0.0] * (6 - len(d)))])
+    fm = None
+    if free_masks is not None:
+        fm = (ctypes.c_uint8 * (6 * n))(*[1 if x else 0 for m in free_masks for x in (list(m) + [0] * (6 - len(m)))])
+    reps = (rve_step_report * n)()
+    st = lib().rve_batch_solve_step(h, de, fm, reps)
+    if raise_on_error:
+        _bcheck(st, h)
+    return st, list(reps)
+
+
+def rve_batch_hessp(h, v_ptrs, out_ptrs):
+    n = len(v_ptrs)
+    vs = (ctypes.c_void_p * n)(*v_ptrs)
+    os_ = (ctypes.c_void_p * n)(*out_ptrs)
+    _bcheck(lib().rve_batch_hessp(h, vs, os_), h)
+
+
+def rve_batch_set_damage(h, i, damage_ptr):
+    _bcheck(lib().rve_batch_set_damage(h, i, ctypes.c_void_p(damage_ptr)), h)
+
+
+def rve_batch_get_state(h, i, strain_ptr=0, kappa_ptr=0, stress_ptr=0, damage_ptr=0):
+    _bcheck(lib().rve_batch_get_state(h, i, ctypes.c_void_p(strain_ptr or None), ctypes.c_void_p(kappa_ptr or None),
+                                      ctypes.c_void_p(stress_ptr or None), ctypes.c_void_p(damage_ptr or None)), h)
+
+
+def rve_batch_reset(h):
+    _bcheck(lib().rve_batch_reset(h), h)
+
+
+def rve_batch_hv_count(h):
+    return lib().rve_batch_hv_count(h)
+
+
+def rve_batch_launch_count(h):
+    return lib().rve_batch_launch_count(h)
+
+
+def rve_batch_destroy(h):
+    lib().rve_batch_destroy(h)
 
 
 def rve_last_error(h):

@@ -139,3 +139,78 @@ class RVESolver:
             self.close()
         except Exception:
             pass
+
+
+class RVEBatch:
+    """Many RVEs of uneven sizes (2D / 3D mixed), FP32, solved in lockstep by
+    the batched launches of the library (one persistent launch per pass)."""
+
+    def __init__(self, dims_list, phase_ids_list, phases, stream=None, **opts):
+        if not torch.cuda.is_available():
+            raise RuntimeError("RVEBatch needs a CUDA device (there is no CPU path)")
+        self.dims = [tuple(int(x) for x in d) for d in dims_list]
+        self.n = len(self.dims)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.shapes = [tuple(reversed(d)) for d in self.dims]
+        self.ncomp = [3 if len(d) == 2 else 6 for d in self.dims]
+        self._ids = []
+        for ids, shp in zip(phase_ids_list, self.shapes):
+            t = torch.as_tensor(ids, dtype=torch.uint8).to(self.device).contiguous()
+            if tuple(t.shape) != shp:
+                raise ValueError(f"phase_ids shape {tuple(t.shape)} != grid {shp}")
+            self._ids.append(t)
+        self.phases = [p if isinstance(p, Phase) else Phase(*p) for p in phases]
+        self.opts = make_opts(32, **opts)
+        self.h = B.rve_batch_create(self.dims, [t.data_ptr() for t in self._ids],
+                                    [p.as_tuple() for p in self.phases], self.opts, self.stream.cuda_stream)
+
+    def field(self, i):
+        return torch.empty((self.ncomp[i],) + self.shapes[i], dtype=torch.float32, device=self.device)
+
+    def hessp(self, vs):
+        outs = [self.field(i) for i in range(self.n)]
+        for i, v in enumerate(vs):
+            if v.dtype != torch.float32 or tuple(v.shape) != (self.ncomp[i],) + self.shapes[i] or not v.is_contiguous():
+                raise ValueError(f"member {i}: bad field")
+        B.rve_batch_hessp(self.h, [v.data_ptr() for v in vs], [o.data_ptr() for o in outs])
+        return outs
+
+    def set_damage(self, i, D):
+        B.rve_batch_set_damage(self.h, i, D.contiguous().data_ptr())
+
+    def get_state(self, i):
+        eps, sig = self.field(i), self.field(i)
+        kap = torch.empty(self.shapes[i], dtype=torch.float32, device=self.device)
+        dmg = torch.empty_like(kap)
+        B.rve_batch_get_state(self.h, i, eps.data_ptr(), kap.data_ptr(), sig.data_ptr(), dmg.data_ptr())
+        return {"eps": eps, "sigma": sig, "kappa": kap, "damage": dmg}
+
+    def reset(self):
+        B.rve_batch_reset(self.h)
+
+    def solve_step(self, dE_list, free_masks=None, raise_on_error=True):
+        st, reps = B.rve_batch_solve_step(self.h, dE_list, free_masks, raise_on_error)
+        out = [_report_dict(r) for r in reps]
+        for o in out:
+            o["status"] = st
+        return out
+
+    @property
+    def hv_count(self):
+        return B.rve_batch_hv_count(self.h)
+
+    @property
+    def launch_count(self):
+        return B.rve_batch_launch_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            B.rve_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -62,24 +62,59 @@ __device__ __forceinline__ bool gate_ok(const Gate& gt, const DevScalars* S, int
   }
 }
 
-// Pull the next item of a work list; returns -1 when exhausted.  Uniform
-// across the block.
-__device__ __forceinline__ int next_item(int* counter, int total, int* s_item) {
+// Work lists over the ACTIVE members only, rebuilt on the device by
+// kb_compact before every gated operation (so a launch enumerates the items
+// of the members that take part, however many members are idle).
+struct WLists {
+  int count;                          // active members
+  int total[BP_N];                    // active items per pass
+  int idx[kMaxBatch];                 // member id of the k-th active member
+  int start[BP_N][kMaxBatch + 1];     // item prefix over active members
+};
+
+// Pull the next item of pass `pass`; false when exhausted.  Uniform across
+// the block.  *v is the item's index (also its partial-sum slot).
+__device__ __forceinline__ bool fetch(const WLists* __restrict__ wl, int pass, int* counter, int* s_item, int* v,
+                                      int* member, int* local) {
   __syncthreads();
   if (threadIdx.x == 0) *s_item = atomicAdd(counter, 1);
   __syncthreads();
-  const int v = *s_item;
-  return v < total ? v : -1;
-}
-
-__device__ __forceinline__ int owner_of(const int* __restrict__ start, int n, int v) {
-  int lo = 0, hi = n - 1;
+  const int it = *s_item;
+  if (it >= wl->total[pass]) return false;
+  const int* st = wl->start[pass];
+  int lo = 0, hi = wl->count - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (start[mid] <= v) lo = mid;
+    if (st[mid] <= it) lo = mid;
     else hi = mid - 1;
   }
-  return lo;
+  *v = it;
+  *member = wl->idx[lo];
+  *local = it - st[lo];
+  return true;
+}
+
+// One block: the members passing the gate, in order, and their item
+// prefixes for every pass (nb: BP_N x n block counts).
+__global__ void kb_compact(WLists* wl, const int* __restrict__ nb, int n, Gate gt, const DevScalars* S) {
+  __shared__ int flag[kMaxBatch];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) flag[i] = gate_ok(gt, S, i) ? 1 : 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int k = 0;
+    for (int i = 0; i < n; ++i)
+      if (flag[i]) wl->idx[k++] = i;
+    wl->count = k;
+    for (int p = 0; p < BP_N; ++p) {
+      int sum = 0;
+      for (int q = 0; q < k; ++q) {
+        wl->start[p][q] = sum;
+        sum += nb[p * n + wl->idx[q]];
+      }
+      wl->start[p][k] = sum;
+      wl->total[p] = sum;
+    }
+  }
 }
 
 // ------------------------------------------------------ spectral passes
@@ -87,33 +122,28 @@ __device__ __forceinline__ int owner_of(const int* __restrict__ start, int n, in
 // DOT for the x-inverse: 0 none, 1 with dotw, 2 self.
 template <int XMODE>
 __global__ void __launch_bounds__(kXThreads)
-    kb_xfwd(const BDesc* __restrict__ D, const int* __restrict__ start, int n, int total, int* counter, Gate gt,
+    kb_xfwd(const BDesc* __restrict__ D, const WLists* __restrict__ wl, int* counter,
             const DevScalars* __restrict__ S, const MatTable<R> mt, const R* __restrict__ in,
             const uint8_t* __restrict__ phase, const R* __restrict__ dmg) {
   __shared__ int s_item;
   for (;;) {
-    const int v = next_item(counter, total, &s_item);
-    if (v < 0) break;
-    const int i = owner_of(start, n, v);
-    if (!gate_ok(gt, S, i)) continue;
+    int v, i, lb;
+    if (!fetch(wl, BP_X, counter, &s_item, &v, &i, &lb)) break;
     const BDesc& d = D[i];
     xfwd_body<R, XMODE>(in + d.foff, phase + d.voff, dmg + d.voff, mt, d.spec, d.g, d.qx, d.px, d.tw[0],
-                        v - start[i]);
+                        lb);
   }
 }
 
 template <bool YINV>
 __global__ void __launch_bounds__(kYThreads)
-    kb_ycols(const BDesc* __restrict__ D, const int* __restrict__ start, int n, int total, int* counter, Gate gt,
-             const DevScalars* __restrict__ S) {
+    kb_ycols(const BDesc* __restrict__ D, const WLists* __restrict__ wl, int* counter) {
   __shared__ int s_item;
   for (;;) {
-    const int v = next_item(counter, total, &s_item);
-    if (v < 0) break;
-    const int i = owner_of(start, n, v);
-    if (!gate_ok(gt, S, i)) continue;
+    int v, i, lb;
+    if (!fetch(wl, BP_Y, counter, &s_item, &v, &i, &lb)) break;
     const BDesc& d = D[i];
-    const int b = v - start[i];
+    const int b = lb;
     const int nbx = (d.g.nxh + d.ty - 1) / d.ty;
     const int bx = b % nbx, rest = b / nbx;
     ycols_body<R, YINV>(d.spec, d.g, d.ty, d.py, d.tw[1], bx, rest % d.g.nz, rest / d.g.nz);
@@ -121,16 +151,13 @@ __global__ void __launch_bounds__(kYThreads)
 }
 
 __global__ void __launch_bounds__(kZThreads)
-    kb_zproj(const BDesc* __restrict__ D, const int* __restrict__ start, int n, int total, int* counter, Gate gt,
-             const DevScalars* __restrict__ S) {
+    kb_zproj(const BDesc* __restrict__ D, const WLists* __restrict__ wl, int* counter) {
   __shared__ int s_item;
   for (;;) {
-    const int v = next_item(counter, total, &s_item);
-    if (v < 0) break;
-    const int i = owner_of(start, n, v);
-    if (!gate_ok(gt, S, i)) continue;
+    int v, i, lb;
+    if (!fetch(wl, BP_Z, counter, &s_item, &v, &i, &lb)) break;
     const BDesc& d = D[i];
-    const int b = v - start[i];
+    const int b = lb;
     const int nbx = (d.g.nxh + d.tz - 1) / d.tz;
     zproj_body<R>(d.spec, d.g, d.tz, d.pz, d.tw[2], d.gd[0], d.ga[0], d.gd[1], d.ga[1], d.gd[2], d.ga[2],
                   d.free_mask, b % nbx, b / nbx);
@@ -138,46 +165,42 @@ __global__ void __launch_bounds__(kZThreads)
 }
 
 __global__ void __launch_bounds__(kYThreads)
-    kb_yproj2d(const BDesc* __restrict__ D, const int* __restrict__ start, int n, int total, int* counter, Gate gt,
-               const DevScalars* __restrict__ S) {
+    kb_yproj2d(const BDesc* __restrict__ D, const WLists* __restrict__ wl, int* counter) {
   __shared__ int s_item;
   for (;;) {
-    const int v = next_item(counter, total, &s_item);
-    if (v < 0) break;
-    const int i = owner_of(start, n, v);
-    if (!gate_ok(gt, S, i)) continue;
+    int v, i, lb;
+    if (!fetch(wl, BP_2D, counter, &s_item, &v, &i, &lb)) break;
     const BDesc& d = D[i];
     yproj2d_body<R>(d.spec, d.g, d.tz, d.py, d.tw[1], d.gd[0], d.ga[0], d.gd[1], d.ga[1], d.free_mask,
-                    v - start[i]);
+                    lb);
   }
 }
 
 template <int DOT>
 __global__ void __launch_bounds__(kXThreads)
-    kb_xinv(const BDesc* __restrict__ D, const int* __restrict__ start, int n, int total, int* counter, Gate gt,
+    kb_xinv(const BDesc* __restrict__ D, const WLists* __restrict__ wl, int* counter,
             const DevScalars* __restrict__ S, R* __restrict__ out, const R* __restrict__ dotw,
             double* __restrict__ partials) {
   __shared__ int s_item;
   for (;;) {
-    const int v = next_item(counter, total, &s_item);
-    if (v < 0) break;
-    const int i = owner_of(start, n, v);
-    if (!gate_ok(gt, S, i)) continue;
+    int v, i, lb;
+    if (!fetch(wl, BP_X, counter, &s_item, &v, &i, &lb)) break;
     const BDesc& d = D[i];
     const R scale = (R)(1.0 / (double)d.g.nvox);
     xinv_body<R, DOT != 0>(d.spec, out + d.foff, DOT == 1 ? dotw + d.foff : nullptr,
-                           DOT ? partials + v : nullptr, d.g, d.qx, d.px, d.tw[0], scale, DOT == 2, v - start[i]);
+                           DOT ? partials + v : nullptr, d.g, d.qx, d.px, d.tw[0], scale, DOT == 2, lb);
   }
 }
 
 // Sum per-item partials over each gated RVE's item range into a DevScalars
 // field group (ns consecutive doubles at byte offset `off`).
-__global__ void kb_seg_reduce(const double* __restrict__ part, const int* __restrict__ start, int n, int ns,
-                              DevScalars* S, int off, Gate gt) {
+__global__ void kb_seg_reduce(const double* __restrict__ part, const WLists* __restrict__ wl, int pass, int ns,
+                              DevScalars* S, int off) {
   __shared__ double red[32];
-  const int i = blockIdx.x;
-  if (i >= n || !gate_ok(gt, S, i)) return;
-  const int s0 = start[i], s1 = start[i + 1];
+  const int k = blockIdx.x;
+  if (k >= wl->count) return;
+  const int i = wl->idx[k];
+  const int s0 = wl->start[pass][k], s1 = wl->start[pass][k + 1];
   double* dst = reinterpret_cast<double*>(reinterpret_cast<char*>(&S[i]) + off);
   for (int s = 0; s < ns; ++s) {
     double acc = 0.0;
@@ -194,20 +217,18 @@ enum VecOp : int { V_INIT = 0, V_UPDATE = 1, V_RESTART = 2, V_DUPDATE = 3, V_AXP
 
 template <int OP, int NS>
 __global__ void __launch_bounds__(256)
-    kb_vec(const BDesc* __restrict__ D, const int* __restrict__ start, int n, int total, int* counter, Gate gt,
+    kb_vec(const BDesc* __restrict__ D, const WLists* __restrict__ wl, int* counter,
            DevScalars* __restrict__ S, R* __restrict__ a, R* __restrict__ b, R* __restrict__ c,
            const R* __restrict__ x, const R* __restrict__ y, const double* __restrict__ dE6,
            double* __restrict__ part) {
   __shared__ int s_item;
   __shared__ double red[NS > 0 ? NS * 32 : 32];
   for (;;) {
-    const int v = next_item(counter, total, &s_item);
-    if (v < 0) break;
-    const int i = owner_of(start, n, v);
-    if (!gate_ok(gt, S, i)) continue;
+    int v, i, lb;
+    if (!fetch(wl, BP_VEC, counter, &s_item, &v, &i, &lb)) break;
     const BDesc& d = D[i];
     const long long nf = (long long)d.g.ncomp * d.g.nvox;
-    const long long e0 = (long long)(v - start[i]) * kVecChunk;
+    const long long e0 = (long long)(lb) * kVecChunk;
     const long long e1 = min(nf, e0 + kVecChunk);
     KSum<R> acc[NS > 0 ? NS : 1];
     const DevScalars& s = S[i];
@@ -271,16 +292,14 @@ __global__ void __launch_bounds__(256)
 
 // scalar-field copy (damage, kappa) over voxel items: a = x
 __global__ void __launch_bounds__(256)
-    kb_scopy(const BDesc* __restrict__ D, const int* __restrict__ start, int n, int total, int* counter, Gate gt,
-             const DevScalars* __restrict__ S, R* __restrict__ a, const R* __restrict__ x) {
+    kb_scopy(const BDesc* __restrict__ D, const WLists* __restrict__ wl, int* counter, R* __restrict__ a,
+             const R* __restrict__ x) {
   __shared__ int s_item;
   for (;;) {
-    const int v = next_item(counter, total, &s_item);
-    if (v < 0) break;
-    const int i = owner_of(start, n, v);
-    if (!gate_ok(gt, S, i)) continue;
+    int v, i, lb;
+    if (!fetch(wl, BP_VOX, counter, &s_item, &v, &i, &lb)) break;
     const BDesc& d = D[i];
-    const long long v0 = (long long)(v - start[i]) * kVoxChunk;
+    const long long v0 = (long long)(lb) * kVoxChunk;
     const long long v1 = min(d.g.nvox, v0 + kVoxChunk);
     for (long long k = v0 + threadIdx.x; k < v1; k += blockDim.x) a[d.voff + k] = x[d.voff + k];
   }
@@ -291,8 +310,8 @@ __global__ void __launch_bounds__(256)
 // per component (12 sums).
 template <bool MEANS>
 __global__ void __launch_bounds__(256)
-    kb_trial(const BDesc* __restrict__ D, const int* __restrict__ start, int n, int total, int* counter, Gate gt,
-             const DevScalars* __restrict__ S, const MatTable<R> mt, const uint8_t* __restrict__ phase,
+    kb_trial(const BDesc* __restrict__ D, const WLists* __restrict__ wl, int* counter, const MatTable<R> mt,
+             const uint8_t* __restrict__ phase,
              const R* __restrict__ eps, const R* __restrict__ p, const R* __restrict__ khist,
              const R* __restrict__ sig0, const R* __restrict__ D0, R* __restrict__ sig_t, R* __restrict__ D_t,
              R* __restrict__ kap_t, double* __restrict__ part) {
@@ -300,14 +319,12 @@ __global__ void __launch_bounds__(256)
   constexpr int NS = MEANS ? 12 : 6;
   __shared__ double red[NS * 32];
   for (;;) {
-    const int v = next_item(counter, total, &s_item);
-    if (v < 0) break;
-    const int i = owner_of(start, n, v);
-    if (!gate_ok(gt, S, i)) continue;
+    int v, i, lb;
+    if (!fetch(wl, BP_VOX, counter, &s_item, &v, &i, &lb)) break;
     const BDesc& d = D[i];
     const int nc = d.g.ncomp, nd = d.g.ndim;
     const long long nv = d.g.nvox;
-    const long long v0 = (long long)(v - start[i]) * kVoxChunk;
+    const long long v0 = (long long)(lb) * kVoxChunk;
     const long long v1 = min(nv, v0 + kVoxChunk);
     KSum<R> acc[NS];
     for (long long k = v0 + threadIdx.x; k < v1; k += blockDim.x) {
@@ -431,7 +448,8 @@ struct rve_batch_ctx {
   std::vector<SpecWork<R>> sw;
   std::vector<BDesc> desc;
   BDesc* dD = nullptr;
-  int* dstart[BP_N] = {};
+  int* dnb = nullptr;      // BP_N x n block counts (device)
+  WLists* wl = nullptr;    // compacted work lists (device)
   std::vector<int> hstart[BP_N];
   int total[BP_N] = {};
   size_t smem[BP_N] = {};
@@ -498,8 +516,15 @@ cudaError_t reset_counters(rve_batch_ctx* c) {
   return cudaMemsetAsync(c->counters, 0, c->ncounters * sizeof(int), c->st);
 }
 
-cudaError_t seg_reduce(rve_batch_ctx* c, int pass, int ns, size_t off, Gate gt) {
-  kb_seg_reduce<<<c->n, 256, 0, c->st>>>(c->part, c->dstart[pass], c->n, ns, c->S, (int)off, gt);
+cudaError_t compact(rve_batch_ctx* c, Gate gt) {
+  kb_compact<<<1, 256, 0, c->st>>>(c->wl, c->dnb, c->n, gt, c->S);
+  ++c->launches;
+  return cudaGetLastError();
+}
+
+// per-member sums over the items of the last compacted work list
+cudaError_t seg_reduce(rve_batch_ctx* c, int pass, int ns, size_t off) {
+  kb_seg_reduce<<<c->n, 256, 0, c->st>>>(c->part, c->wl, pass, ns, c->S, (int)off);
   ++c->launches;
   return cudaGetLastError();
 }
@@ -509,85 +534,89 @@ cudaError_t seg_reduce(rve_batch_ctx* c, int pass, int ns, size_t off, Gate gt) 
 // dotw == out) into DevScalars at byte offset dot_off.
 cudaError_t batch_apply(rve_batch_ctx* c, const R* in, R* out, bool tangent, const R* dotw, size_t dot_off, Gate gt) {
   cudaError_t e;
+  if ((e = compact(c, gt)) != cudaSuccess) return e;
   {
     const int tot = c->total[BP_X];
     if (tangent)
-      kb_xfwd<1><<<grid_for(tot, 4), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->dstart[BP_X], c->n, tot,
-                                                                        next_counter(c), gt, c->S, c->mt, in,
+      kb_xfwd<1><<<grid_for(tot, 4), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
+                                                                        next_counter(c), c->S, c->mt, in,
                                                                         c->phase, c->D);
     else
-      kb_xfwd<0><<<grid_for(tot, 4), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->dstart[BP_X], c->n, tot,
-                                                                        next_counter(c), gt, c->S, c->mt, in,
+      kb_xfwd<0><<<grid_for(tot, 4), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
+                                                                        next_counter(c), c->S, c->mt, in,
                                                                         c->phase, c->D);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (c->any3d) {
     kb_ycols<false><<<grid_for(c->total[BP_Y], 4), kYThreads, c->smem[BP_Y], c->st>>>(
-        c->dD, c->dstart[BP_Y], c->n, c->total[BP_Y], next_counter(c), gt, c->S);
-    kb_zproj<<<grid_for(c->total[BP_Z], 2), kZThreads, c->smem[BP_Z], c->st>>>(c->dD, c->dstart[BP_Z], c->n,
-                                                                               c->total[BP_Z], next_counter(c),
-                                                                               gt, c->S);
+        c->dD, c->wl, next_counter(c));
+    kb_zproj<<<grid_for(c->total[BP_Z], 2), kZThreads, c->smem[BP_Z], c->st>>>(c->dD, c->wl, next_counter(c));
     kb_ycols<true><<<grid_for(c->total[BP_Y], 4), kYThreads, c->smem[BP_Y], c->st>>>(
-        c->dD, c->dstart[BP_Y], c->n, c->total[BP_Y], next_counter(c), gt, c->S);
+        c->dD, c->wl, next_counter(c));
     c->launches += 3;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (c->any2d) {
     kb_yproj2d<<<grid_for(c->total[BP_2D], 4), kYThreads, c->smem[BP_2D], c->st>>>(
-        c->dD, c->dstart[BP_2D], c->n, c->total[BP_2D], next_counter(c), gt, c->S);
+        c->dD, c->wl, next_counter(c));
     ++c->launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const int tot = c->total[BP_X];
   if (!dotw) {
-    kb_xinv<0><<<grid_for(tot, 4), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->dstart[BP_X], c->n, tot,
-                                                                      next_counter(c), gt, c->S, out, nullptr,
+    kb_xinv<0><<<grid_for(tot, 4), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
+                                                                      next_counter(c), c->S, out, nullptr,
                                                                       nullptr);
   } else if (dotw == out) {
-    kb_xinv<2><<<grid_for(tot, 4), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->dstart[BP_X], c->n, tot,
-                                                                      next_counter(c), gt, c->S, out, nullptr,
+    kb_xinv<2><<<grid_for(tot, 4), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
+                                                                      next_counter(c), c->S, out, nullptr,
                                                                       c->part);
   } else {
-    kb_xinv<1><<<grid_for(tot, 4), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->dstart[BP_X], c->n, tot,
-                                                                      next_counter(c), gt, c->S, out, dotw,
+    kb_xinv<1><<<grid_for(tot, 4), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
+                                                                      next_counter(c), c->S, out, dotw,
                                                                       c->part);
   }
   c->launches += 2;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (dotw) return seg_reduce(c, BP_X, 1, dot_off, gt);
+  if (dotw) return seg_reduce(c, BP_X, 1, dot_off);
   return cudaSuccess;
 }
 
 template <int OP, int NS>
 cudaError_t vec(rve_batch_ctx* c, Gate gt, R* a, R* b, R* cc, const R* x, const R* y, size_t sum_off) {
+  cudaError_t e = compact(c, gt);
+  if (e != cudaSuccess) return e;
   const int tot = c->total[BP_VEC];
-  kb_vec<OP, NS><<<grid_for(tot, 8), 256, 0, c->st>>>(c->dD, c->dstart[BP_VEC], c->n, tot, next_counter(c), gt,
-                                                       c->S, a, b, cc, x, y, c->dE, c->part);
+  kb_vec<OP, NS><<<grid_for(tot, 8), 256, 0, c->st>>>(c->dD, c->wl, next_counter(c), c->S, a, b, cc, x, y, c->dE,
+                                                       c->part);
   ++c->launches;
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess || NS == 0) return e;
-  return seg_reduce(c, BP_VEC, NS, sum_off, gt);
+  return seg_reduce(c, BP_VEC, NS, sum_off);
 }
 
 cudaError_t scopy(rve_batch_ctx* c, Gate gt, R* a, const R* x) {
+  cudaError_t e = compact(c, gt);
+  if (e != cudaSuccess) return e;
   const int tot = c->total[BP_VOX];
-  kb_scopy<<<grid_for(tot, 8), 256, 0, c->st>>>(c->dD, c->dstart[BP_VOX], c->n, tot, next_counter(c), gt, c->S,
-                                                a, x);
+  kb_scopy<<<grid_for(tot, 8), 256, 0, c->st>>>(c->dD, c->wl, next_counter(c), a, x);
   ++c->launches;
   return cudaGetLastError();
 }
 
 cudaError_t trial(rve_batch_ctx* c, Gate gt, const R* p, bool with_state) {
+  cudaError_t e0 = compact(c, gt);
+  if (e0 != cudaSuccess) return e0;
   const int tot = c->total[BP_VOX];
-  kb_trial<false><<<grid_for(tot, 8), 256, 0, c->st>>>(c->dD, c->dstart[BP_VOX], c->n, tot, next_counter(c), gt,
-                                                       c->S, c->mt, c->phase, c->eps, p, c->khist,
+  kb_trial<false><<<grid_for(tot, 8), 256, 0, c->st>>>(c->dD, c->wl, next_counter(c), c->mt, c->phase, c->eps, p,
+                                                       c->khist,
                                                        with_state ? c->sig : nullptr, with_state ? c->D : nullptr,
                                                        with_state ? c->sig_t : c->sig, with_state ? c->D_t : c->D,
                                                        with_state ? c->kap_t : c->kap, c->part);
   ++c->launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return seg_reduce(c, BP_VOX, 6, offsetof(DevScalars, sp), gt);
+  return seg_reduce(c, BP_VOX, 6, offsetof(DevScalars, sp));
 }
 
 cudaError_t scalar(rve_batch_ctx* c, int op, Gate gt) {
@@ -808,12 +837,13 @@ rve_status batch_solve(rve_batch_ctx* c, const double* dE, rve_step_report* reps
   BCK(reset_counters(c), "memset");
   {
     const int tot = c->total[BP_VOX];
-    kb_trial<true><<<grid_for(tot, 8), 256, 0, c->st>>>(c->dD, c->dstart[BP_VOX], n, tot, next_counter(c), ga,
-                                                        c->S, c->mt, c->phase, c->eps, nullptr, c->khist, c->sig,
-                                                        nullptr, nullptr, nullptr, nullptr, c->part);
+    BCK(compact(c, ga), "means");
+    kb_trial<true><<<grid_for(tot, 8), 256, 0, c->st>>>(c->dD, c->wl, next_counter(c), c->mt, c->phase, c->eps,
+                                                        nullptr, c->khist, c->sig, nullptr, nullptr, nullptr,
+                                                        nullptr, c->part);
     ++c->launches;
     BCK(cudaGetLastError(), "means");
-    BCK(seg_reduce(c, BP_VOX, 12, offsetof(DevScalars, msig), ga), "means");
+    BCK(seg_reduce(c, BP_VOX, 12, offsetof(DevScalars, msig)), "means");
   }
   BCK(scopy(c, gate_bits(conv), c->khist, c->kap), "commit");
   if ((s = read_all(c)) != RVE_OK) return s;
@@ -839,8 +869,8 @@ void batch_free(rve_batch_ctx* c) {
                   c->D, c->D_t, c->kap, c->kap_t, c->khist, c->phase, c->S, c->part, c->dE, c->dR};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  for (int p = 0; p < BP_N; ++p)
-    if (c->dstart[p]) cudaFree(c->dstart[p]);
+  if (c->dnb) cudaFree(c->dnb);
+  if (c->wl) cudaFree(c->wl);
   if (c->Sh) cudaFreeHost(c->Sh);
   if (c->hbuf) cudaFreeHost(c->hbuf);
   if (c->g_iter) cudaGraphExecDestroy(c->g_iter);
@@ -917,11 +947,14 @@ rve_status batch_init(rve_batch_ctx* c, const int* dims, const int* ndims, const
       c->smem[BP_2D] = std::max(c->smem[BP_2D], (size_t)3 * w.tz * g.ny * sizeof(C));
     }
   }
+  std::vector<int> nbh((size_t)BP_N * n);
   for (int p = 0; p < BP_N; ++p) {
     c->total[p] = c->hstart[p][n];
-    BCK(cudaMalloc(&c->dstart[p], (n + 1) * sizeof(int)), "schedule");
-    BCK(cudaMemcpy(c->dstart[p], c->hstart[p].data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice), "schedule");
+    for (int i = 0; i < n; ++i) nbh[(size_t)p * n + i] = c->hstart[p][i + 1] - c->hstart[p][i];
   }
+  BCK(cudaMalloc(&c->dnb, nbh.size() * sizeof(int)), "schedule");
+  BCK(cudaMemcpy(c->dnb, nbh.data(), nbh.size() * sizeof(int), cudaMemcpyHostToDevice), "schedule");
+  BCK(cudaMalloc(&c->wl, sizeof(WLists)), "work lists");
   BCK(cudaMalloc(&c->dD, n * sizeof(BDesc)), "descriptors");
   BCK(cudaMemcpy(c->dD, c->desc.data(), n * sizeof(BDesc), cudaMemcpyHostToDevice), "descriptors");
   BCK(cudaMalloc(&c->counters, c->ncounters * sizeof(int)), "counters");

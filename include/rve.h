@@ -235,6 +235,48 @@ long long rve_batch_hv_count(rve_batch_t);
 long long rve_batch_launch_count(rve_batch_t);
 void rve_batch_destroy(rve_batch_t);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start: a spectral neural operator that proposes the next
+ * load step's strain-fluctuation increment (the paper has no learned part;
+ * the proposal only seeds the trust-region solve, which still decides
+ * convergence).  Inputs channels last [B][Nz][Ny][Nx][cin] (phase one-hot,
+ * damage, previous two fluctuation increments), output [..][cout].
+ * Network: lift, `layers` Fourier layers of width 32 (retained modes kx in
+ * [0, modes), ky, kz in [-modes/2, modes/2); per-mode real 64 x 64 maps of
+ * the (Re, Im) channel pairs, BF16; GELU between layers), projection.  All
+ * contractions on the tensor cores (BF16 operands, FP32 accumulation).
+ * Parameters are one packed FP32 vector: Wl (cin x 32, [in][out]), bl (32),
+ * per layer W (32 x 32, [in][out]), b (32), R (modes^3 x 64 x 64), then Wq
+ * (32 x cout, [in][out]), bq (cout).
+ * ------------------------------------------------------------------------ */
+typedef struct rve_fno_ctx* rve_fno_t;
+rve_status rve_fno_create(int cin, int width, int cout, int layers, int modes, unsigned long long seed,
+                          void* stream, rve_fno_t* out);
+long long rve_fno_param_count(rve_fno_t);
+/* Replace the parameters (host, packed) and reset the optimiser state. */
+rve_status rve_fno_set_params(rve_fno_t, const float* params_host);
+/* Copy out the parameters and / or the last gradient (host, packed; NULL skips). */
+rve_status rve_fno_get_params(rve_fno_t, float* params_host, float* grad_host);
+/* y = net(x) for batch <= 8 samples of grid dims (Nx, Ny, Nz); Nx >= 2 modes
+ * (no retained mode at or above the real axis' Nyquist index), Ny, Nz >= modes. */
+rve_status rve_fno_forward(rve_fno_t, int batch, const int dims[3], const float* x_dev, float* y_dev);
+/* Mean-squared-error loss against targets t and its gradient (kept for the
+ * next rve_fno_adam_step, readable with rve_fno_get_params).  Synchronises. */
+rve_status rve_fno_loss_grad(rve_fno_t, int batch, const int dims[3], const float* x_dev, const float* t_dev,
+                             double* loss_host);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr. */
+rve_status rve_fno_adam_step(rve_fno_t, double lr);
+/* Build the input features of one sample from solver fields (FP32 SoA):
+ * phase ids, damage (may be NULL), previous two fluctuation increments
+ * (6 x Nvox each, may be NULL), scaled by `scale`.  Needs cin >= 15. */
+rve_status rve_fno_pack_features(rve_fno_t, const int dims[3], const uint8_t* phase_dev, const float* damage_dev,
+                                 const float* d1_dev, const float* d2_dev, float scale, float* x_dev);
+/* Channels-last output of one sample -> SoA Mandel field times `scale`. */
+rve_status rve_fno_unpack_output(rve_fno_t, const int dims[3], const float* y_dev, float scale, float* out_dev);
+const char* rve_fno_last_error(rve_fno_t);
+long long rve_fno_launch_count(rve_fno_t);
+void rve_fno_destroy(rve_fno_t);
+
 /* Message of the last error on this context (static storage; never NULL). */
 const char* rve_last_error(rve_t);
 

@@ -81,6 +81,24 @@ _SIGS = [
     ("rve_batch_hv_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("rve_batch_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("rve_batch_destroy", None, [ctypes.c_void_p]),
+    ("rve_fno_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_ulonglong, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("rve_fno_param_count", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("rve_fno_set_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("rve_fno_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("rve_fno_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    ("rve_fno_loss_grad", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    ("rve_fno_adam_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    ("rve_fno_pack_features", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float,
+                                             ctypes.c_void_p]),
+    ("rve_fno_unpack_output", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
+                                             ctypes.c_float, ctypes.c_void_p]),
+    ("rve_fno_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("rve_fno_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("rve_fno_destroy", None, [ctypes.c_void_p]),
     ("rve_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("rve_hv_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("rve_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
@@ -266,6 +284,67 @@ def rve_batch_launch_count(h):
 
 def rve_batch_destroy(h):
     lib().rve_batch_destroy(h)
+
+
+def _fcheck(status, handle):
+    if status != RVE_OK:
+        raise RveError(status, lib().rve_fno_last_error(handle).decode())
+
+
+def _dims3(dims):
+    return (ctypes.c_int * 3)(*(list(dims) + [1] * (3 - len(dims))))
+
+
+def rve_fno_create(cin, width, cout, layers, modes, seed=0, stream=0):
+    h = ctypes.c_void_p()
+    _fcheck(lib().rve_fno_create(cin, width, cout, layers, modes, seed, ctypes.c_void_p(stream), ctypes.byref(h)),
+            None)
+    return h
+
+
+def rve_fno_param_count(h):
+    return lib().rve_fno_param_count(h)
+
+
+def rve_fno_set_params(h, params_ptr):
+    _fcheck(lib().rve_fno_set_params(h, ctypes.c_void_p(params_ptr)), h)
+
+
+def rve_fno_get_params(h, params_ptr=0, grad_ptr=0):
+    _fcheck(lib().rve_fno_get_params(h, ctypes.c_void_p(params_ptr or None), ctypes.c_void_p(grad_ptr or None)), h)
+
+
+def rve_fno_forward(h, batch, dims, x_ptr, y_ptr):
+    _fcheck(lib().rve_fno_forward(h, batch, _dims3(dims), ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr)), h)
+
+
+def rve_fno_loss_grad(h, batch, dims, x_ptr, t_ptr):
+    loss = ctypes.c_double()
+    _fcheck(lib().rve_fno_loss_grad(h, batch, _dims3(dims), ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr),
+                                    ctypes.byref(loss)), h)
+    return loss.value
+
+
+def rve_fno_adam_step(h, lr):
+    _fcheck(lib().rve_fno_adam_step(h, lr), h)
+
+
+def rve_fno_pack_features(h, dims, phase_ptr, damage_ptr, d1_ptr, d2_ptr, scale, x_ptr):
+    _fcheck(lib().rve_fno_pack_features(h, _dims3(dims), ctypes.c_void_p(phase_ptr), ctypes.c_void_p(damage_ptr or None),
+                                        ctypes.c_void_p(d1_ptr or None), ctypes.c_void_p(d2_ptr or None),
+                                        scale, ctypes.c_void_p(x_ptr)), h)
+
+
+def rve_fno_unpack_output(h, dims, y_ptr, scale, out_ptr):
+    _fcheck(lib().rve_fno_unpack_output(h, _dims3(dims), ctypes.c_void_p(y_ptr), scale, ctypes.c_void_p(out_ptr)), h)
+
+
+def rve_fno_launch_count(h):
+    return lib().rve_fno_launch_count(h)
+
+
+def rve_fno_destroy(h):
+    lib().rve_fno_destroy(h)
 
 
 def rve_last_error(h):

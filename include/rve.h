@@ -268,11 +268,28 @@ rve_status rve_fno_loss_grad(rve_fno_t, int batch, const int dims[3], const floa
 rve_status rve_fno_adam_step(rve_fno_t, double lr);
 /* Build the input features of one sample from solver fields (FP32 SoA):
  * phase ids, damage (may be NULL), previous two fluctuation increments
- * (6 x Nvox each, may be NULL), scaled by `scale`.  Needs cin >= 15. */
+ * (6 x Nvox each, may be NULL) scaled by `scale`, and, in channel 15 when
+ * cin >= 16, the history variable kappa (may be NULL) times kappa_scale.
+ * Needs cin >= 15. */
 rve_status rve_fno_pack_features(rve_fno_t, const int dims[3], const uint8_t* phase_dev, const float* damage_dev,
-                                 const float* d1_dev, const float* d2_dev, float scale, float* x_dev);
-/* Channels-last output of one sample -> SoA Mandel field times `scale`. */
-rve_status rve_fno_unpack_output(rve_fno_t, const int dims[3], const float* y_dev, float scale, float* out_dev);
+                                 const float* kappa_dev, float kappa_scale, const float* d1_dev, const float* d2_dev,
+                                 float scale, float* x_dev);
+/* Channels-last output of one sample -> SoA Mandel field:
+ * out = base + scale * y (base, a SoA field, may be NULL; with base = the
+ * last fluctuation increment the network predicts the change of the
+ * increment). */
+rve_status rve_fno_unpack_output(rve_fno_t, const int dims[3], const float* y_dev, float scale, const float* base_dev,
+                                 float* out_dev);
+/* SoA Mandel fields (cout x Nvox) -> channels-last training target
+ * t = scale * (field - base) [Nz][Ny][Nx][cout] (base may be NULL; the
+ * inverse of rve_fno_unpack_output). */
+rve_status rve_fno_pack_target(rve_fno_t, const int dims[3], const float* field_dev, const float* base_dev, float scale,
+                               float* t_dev);
+/* Fluctuation increment between two converged FP32 strain fields (cout x
+ * Nvox each): out = eps_new - eps_old - dE (dE uniform per Mandel component,
+ * the applied mean-strain increment of the step). */
+rve_status rve_fno_increment(rve_fno_t, const int dims[3], const float* eps_new_dev, const float* eps_old_dev,
+                             const double dE_host[6], float* out_dev);
 const char* rve_fno_last_error(rve_fno_t);
 long long rve_fno_launch_count(rve_fno_t);
 void rve_fno_destroy(rve_fno_t);

@@ -92,10 +92,14 @@ _SIGS = [
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     ("rve_fno_adam_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     ("rve_fno_pack_features", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
-                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float,
-                                             ctypes.c_void_p]),
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p]),
     ("rve_fno_unpack_output", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
-                                             ctypes.c_float, ctypes.c_void_p]),
+                                             ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
+    ("rve_fno_pack_target", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p]),
+    ("rve_fno_increment", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     ("rve_fno_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("rve_fno_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("rve_fno_destroy", None, [ctypes.c_void_p]),
@@ -329,14 +333,27 @@ def rve_fno_adam_step(h, lr):
     _fcheck(lib().rve_fno_adam_step(h, lr), h)
 
 
-def rve_fno_pack_features(h, dims, phase_ptr, damage_ptr, d1_ptr, d2_ptr, scale, x_ptr):
+def rve_fno_pack_features(h, dims, phase_ptr, damage_ptr, d1_ptr, d2_ptr, scale, x_ptr, kappa_ptr=0, kappa_scale=1.0):
     _fcheck(lib().rve_fno_pack_features(h, _dims3(dims), ctypes.c_void_p(phase_ptr), ctypes.c_void_p(damage_ptr or None),
+                                        ctypes.c_void_p(kappa_ptr or None), kappa_scale,
                                         ctypes.c_void_p(d1_ptr or None), ctypes.c_void_p(d2_ptr or None),
                                         scale, ctypes.c_void_p(x_ptr)), h)
 
 
-def rve_fno_unpack_output(h, dims, y_ptr, scale, out_ptr):
-    _fcheck(lib().rve_fno_unpack_output(h, _dims3(dims), ctypes.c_void_p(y_ptr), scale, ctypes.c_void_p(out_ptr)), h)
+def rve_fno_unpack_output(h, dims, y_ptr, scale, out_ptr, base_ptr=0):
+    _fcheck(lib().rve_fno_unpack_output(h, _dims3(dims), ctypes.c_void_p(y_ptr), scale,
+                                        ctypes.c_void_p(base_ptr or None), ctypes.c_void_p(out_ptr)), h)
+
+
+def rve_fno_pack_target(h, dims, field_ptr, scale, t_ptr, base_ptr=0):
+    _fcheck(lib().rve_fno_pack_target(h, _dims3(dims), ctypes.c_void_p(field_ptr), ctypes.c_void_p(base_ptr or None),
+                                      scale, ctypes.c_void_p(t_ptr)), h)
+
+
+def rve_fno_increment(h, dims, new_ptr, old_ptr, dE, out_ptr):
+    d = (ctypes.c_double * 6)(*(list(dE) + [0.0] * (6 - len(dE))))
+    _fcheck(lib().rve_fno_increment(h, _dims3(dims), ctypes.c_void_p(new_ptr), ctypes.c_void_p(old_ptr), d,
+                                    ctypes.c_void_p(out_ptr)), h)
 
 
 def rve_fno_launch_count(h):

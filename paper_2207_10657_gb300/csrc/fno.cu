@@ -353,10 +353,11 @@ __global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restric
 
 // Features for the warm start, channels last [Nz][Ny][Nx][cin]: phase
 // one-hot (2), damage (1), previous two fluctuation increments (SoA Mandel
-// fields, ncomp each) times `scale`; remaining channels zero.
-__global__ void k_pack(const uint8_t* __restrict__ phase, const float* __restrict__ dmg, const float* __restrict__ d1,
-                       const float* __restrict__ d2, long long nvox, int nc, float scale, int cin,
-                       float* __restrict__ X) {
+// fields, ncomp each) times `scale`, then (if given and cin > 3 + 2 ncomp)
+// the history variable kappa times `kscale`; remaining channels zero.
+__global__ void k_pack(const uint8_t* __restrict__ phase, const float* __restrict__ dmg, const float* __restrict__ kap,
+                       float kscale, const float* __restrict__ d1, const float* __restrict__ d2, long long nvox, int nc,
+                       float scale, int cin, float* __restrict__ X) {
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
     float* x = X + v * cin;
     const int ph = phase[v];
@@ -366,14 +367,32 @@ __global__ void k_pack(const uint8_t* __restrict__ phase, const float* __restric
     x[k++] = dmg ? dmg[v] : 0.f;
     for (int c = 0; c < nc; ++c) x[k++] = d1 ? d1[c * nvox + v] * scale : 0.f;
     for (int c = 0; c < nc; ++c) x[k++] = d2 ? d2[c * nvox + v] * scale : 0.f;
+    if (k < cin) x[k++] = kap ? kap[v] * kscale : 0.f;
     for (; k < cin; ++k) x[k] = 0.f;
   }
 }
 
-// channels-last [V][cout] -> SoA [cout][V] times `scale`
-__global__ void k_unpack(const float* __restrict__ Y, long long nvox, int cout, float scale, float* __restrict__ out) {
+// channels-last [V][cout] -> SoA [cout][V]: out = base + scale * Y (base may be NULL)
+__global__ void k_unpack(const float* __restrict__ Y, const float* __restrict__ base, long long nvox, int cout,
+                         float scale, float* __restrict__ out) {
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x)
-    for (int c = 0; c < cout; ++c) out[c * nvox + v] = Y[v * cout + c] * scale;
+    for (int c = 0; c < cout; ++c) out[c * nvox + v] = (base ? base[c * nvox + v] : 0.f) + Y[v * cout + c] * scale;
+}
+
+// SoA [cout][V] -> channels-last [V][cout]: T = scale * (f - base) (training targets; base may be NULL)
+__global__ void k_pack_target(const float* __restrict__ f, const float* __restrict__ base, long long nvox, int cout,
+                              float scale, float* __restrict__ T) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x)
+    for (int c = 0; c < cout; ++c) T[v * cout + c] = (f[c * nvox + v] - (base ? base[c * nvox + v] : 0.f)) * scale;
+}
+
+// fluctuation increment: out = eps_new - eps_old - dE (uniform per component)
+__global__ void k_incr(const float* __restrict__ a, const float* __restrict__ b, long long nvox, int ncomp, float d0,
+                       float d1, float d2, float d3, float d4, float d5, float* __restrict__ out) {
+  const float dE[6] = {d0, d1, d2, d3, d4, d5};
+  const long long n = nvox * ncomp;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = a[i] - b[i] - dE[i / nvox];
 }
 
 int nblk(long long n) { return (int)std::min<long long>((n + 255) / 256, 152 * 16); }
@@ -865,22 +884,47 @@ rve_status rve_fno_adam_step(rve_fno_t c, double lr) {
 }
 
 rve_status rve_fno_pack_features(rve_fno_t c, const int dims[3], const uint8_t* phase_dev, const float* damage_dev,
-                                 const float* d1_dev, const float* d2_dev, float scale, float* x_dev) {
+                                 const float* kappa_dev, float kappa_scale, const float* d1_dev, const float* d2_dev,
+                                 float scale, float* x_dev) {
   if (!c || !dims || !phase_dev || !x_dev) return RVE_ERR_ARG;
   if (c->cin < 15) return ffail(c, RVE_ERR_ARG, "feature packing needs cin >= 15");
   const long long V = (long long)dims[0] * dims[1] * dims[2];
-  k_pack<<<nblk(V), 256, 0, c->st>>>(phase_dev, damage_dev, d1_dev, d2_dev, V, 6, scale, c->cin, x_dev);
+  k_pack<<<nblk(V), 256, 0, c->st>>>(phase_dev, damage_dev, kappa_dev, kappa_scale, d1_dev, d2_dev, V, 6, scale,
+                                     c->cin, x_dev);
   ++c->launches;
   FCK(cudaGetLastError(), "pack");
   return RVE_OK;
 }
 
-rve_status rve_fno_unpack_output(rve_fno_t c, const int dims[3], const float* y_dev, float scale, float* out_dev) {
+rve_status rve_fno_unpack_output(rve_fno_t c, const int dims[3], const float* y_dev, float scale, const float* base_dev,
+                                 float* out_dev) {
   if (!c || !dims || !y_dev || !out_dev) return RVE_ERR_ARG;
   const long long V = (long long)dims[0] * dims[1] * dims[2];
-  k_unpack<<<nblk(V), 256, 0, c->st>>>(y_dev, V, c->cout, scale, out_dev);
+  k_unpack<<<nblk(V), 256, 0, c->st>>>(y_dev, base_dev, V, c->cout, scale, out_dev);
   ++c->launches;
   FCK(cudaGetLastError(), "unpack");
+  return RVE_OK;
+}
+
+rve_status rve_fno_pack_target(rve_fno_t c, const int dims[3], const float* field_dev, const float* base_dev, float scale,
+                               float* t_dev) {
+  if (!c || !dims || !field_dev || !t_dev) return RVE_ERR_ARG;
+  const long long V = (long long)dims[0] * dims[1] * dims[2];
+  k_pack_target<<<nblk(V), 256, 0, c->st>>>(field_dev, base_dev, V, c->cout, scale, t_dev);
+  ++c->launches;
+  FCK(cudaGetLastError(), "pack target");
+  return RVE_OK;
+}
+
+rve_status rve_fno_increment(rve_fno_t c, const int dims[3], const float* eps_new_dev, const float* eps_old_dev,
+                             const double dE_host[6], float* out_dev) {
+  if (!c || !dims || !eps_new_dev || !eps_old_dev || !dE_host || !out_dev) return RVE_ERR_ARG;
+  const long long V = (long long)dims[0] * dims[1] * dims[2];
+  k_incr<<<nblk(V * c->cout), 256, 0, c->st>>>(eps_new_dev, eps_old_dev, V, c->cout, (float)dE_host[0],
+                                                (float)dE_host[1], (float)dE_host[2], (float)dE_host[3],
+                                                (float)dE_host[4], (float)dE_host[5], out_dev);
+  ++c->launches;
+  FCK(cudaGetLastError(), "increment");
   return RVE_OK;
 }
 

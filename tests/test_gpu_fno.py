@@ -100,18 +100,37 @@ def test_feature_packing_and_unpacking():
     dm = rng.random(V).astype(np.float32)
     d1 = rng.standard_normal((6, V)).astype(np.float32)
     d2 = rng.standard_normal((6, V)).astype(np.float32)
+    kp = rng.random(V).astype(np.float32)
     X = net.features(dims, torch.from_numpy(ph).cuda(), torch.from_numpy(dm).cuda(), torch.from_numpy(d1).cuda(),
-                     torch.from_numpy(d2).cuda(), 2.0).cpu().numpy().reshape(V, 16)
+                     torch.from_numpy(d2).cuda(), 2.0, torch.from_numpy(kp).cuda(), 4.0).cpu().numpy().reshape(V, 16)
     ref = np.zeros((V, 16), np.float32)
     ref[:, 0] = ph == 0
     ref[:, 1] = ph == 1
     ref[:, 2] = dm
     ref[:, 3:9] = 2.0 * d1.T
     ref[:, 9:15] = 2.0 * d2.T
+    ref[:, 15] = 4.0 * kp
     assert np.array_equal(X, ref)
     Y = rng.standard_normal((1, 5, 7, 10, 6)).astype(np.float32)
     out = net.to_field(torch.from_numpy(Y).cuda(), dims, 0.5).cpu().numpy()
     assert np.array_equal(out.reshape(6, V), 0.5 * Y.reshape(V, 6).T)
+    base = torch.from_numpy(d1.reshape(6, 5, 7, 10)).cuda()
+    out = net.to_field(torch.from_numpy(Y).cuda(), dims, 0.5, base).cpu().numpy()
+    assert np.allclose(out.reshape(6, V), d1 + 0.5 * Y.reshape(V, 6).T, rtol=1e-6, atol=1e-6)
+    # targets: the inverse map, with and without a base field
+    from paper_2207_10657_gb300 import binding as B
+    f = torch.from_numpy(d2.reshape(6, 5, 7, 10)).cuda()
+    T = torch.empty((1, 5, 7, 10, 6), device="cuda")
+    B.rve_fno_pack_target(net.h, dims, f.data_ptr(), 2.0, T.data_ptr())
+    assert np.array_equal(T.cpu().numpy().reshape(V, 6), 2.0 * d2.T)
+    B.rve_fno_pack_target(net.h, dims, f.data_ptr(), 2.0, T.data_ptr(), base.data_ptr())
+    assert np.allclose(T.cpu().numpy().reshape(V, 6), 2.0 * (d2 - d1).T, rtol=1e-6, atol=1e-6)
+    # fluctuation increment between two strain fields
+    inc = torch.empty_like(f)
+    B.rve_fno_increment(net.h, dims, f.data_ptr(), base.data_ptr(), [0, 0, 1e-3, 0, 0, 0], inc.data_ptr())
+    ref = (d2 - d1).copy()
+    ref[2] -= np.float32(1e-3)
+    assert np.allclose(inc.cpu().numpy().reshape(6, V), ref, rtol=1e-6, atol=1e-6)
     net.close()
 
 

@@ -113,7 +113,9 @@ __global__ void __launch_bounds__(kFT)
   __shared__ __align__(16) float2 buf[NL * N];
   __shared__ double red[32];
   const long long row0 = (long long)blockIdx.x * Q;
-  constexpr int LITEMS = NL * N;
+  // each half-spectrum entry kk of the two real lines packed in line p is
+  // read once and fills both buf[kk] and buf[N - kk] (Hermitian symmetry)
+  constexpr int LITEMS = NL * NXH;
   constexpr int LSTEPS = (LITEMS + kFT - 1) / kFT;
   constexpr int LB = LSTEPS < 4 ? LSTEPS : 4;
   for (int s0 = 0; s0 < LSTEPS; s0 += LB) {
@@ -121,8 +123,7 @@ __global__ void __launch_bounds__(kFT)
 #pragma unroll
     for (int b = 0; b < LB; ++b) {
       const int idx = threadIdx.x + (s0 + b) * kFT;
-      const int p = idx / N, k = idx - (idx / N) * N;
-      const int kk = k <= HALF ? k : N - k;
+      const int p = idx / NXH, kk = idx - (idx / NXH) * NXH;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int rho = 2 * p + h;
@@ -136,14 +137,14 @@ __global__ void __launch_bounds__(kFT)
     for (int b = 0; b < LB; ++b) {
       const int idx = threadIdx.x + (s0 + b) * kFT;
       if (s0 + b < LSTEPS && idx < LITEMS) {
-        const int p = idx / N, k = idx - (idx / N) * N;
-        const int kk = k <= HALF ? k : N - k;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (kk == 0 || kk == HALF) xh[b][h].y = 0.f;
-          if (k > HALF) xh[b][h].y = -xh[b][h].y;
+        const int p = idx / NXH, kk = idx - (idx / NXH) * NXH;
+        float2 a = xh[b][0], c2 = xh[b][1];
+        if (kk == 0 || kk == HALF) {
+          a.y = 0.f;
+          c2.y = 0.f;
         }
-        buf[k * NL + p] = make_float2(xh[b][0].x - xh[b][1].y, xh[b][0].y + xh[b][1].x);
+        buf[kk * NL + p] = make_float2(a.x - c2.y, a.y + c2.x);
+        if (kk != 0 && kk != HALF) buf[(N - kk) * NL + p] = make_float2(a.x + c2.y, c2.x - a.y);
       }
     }
   }

@@ -71,6 +71,9 @@ def _args():
                    help="warmstart: time budget of the training-data generation (plain solves at 64^3)")
     p.add_argument("--ws-iters", type=int, default=4000, help="warmstart: Adam iterations")
     p.add_argument("--ws-eval", default="128,128,192", help="warmstart: held-out evaluation grids")
+    p.add_argument("--probe", choices=["step", "fno"], default=None,
+                   help="untimed small case for profilers: 'step' = one load step of a 256x256x128 sphere cell, "
+                        "'fno' = three training iterations of the spectral neural operator at 64^3, batch 4")
     p.add_argument("--batch-max-nr", type=int, default=50,
                    help="Newton cap per member for batch96 (bounds the work of members that localise)")
     return p.parse_args()
@@ -228,6 +231,9 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------ GPU arm
+HV_PASSES = ("xfwd_tangent", "y_fwd", "z_proj", "y_inv", "x_inv")
+
+
 def _pass_bytes(n, pass_name):
     """Algorithmic (compulsory) DRAM bytes of one launch of a pass at n^3, FP32."""
     nvox = n ** 3
@@ -238,7 +244,7 @@ def _pass_bytes(n, pass_name):
         "y_fwd": 2 * spec,
         "z_proj": 2 * spec,
         "y_inv": 2 * spec,
-        "x_inv": spec + field,
+        "x_inv": spec + 2 * field,  # with the fused CG dot product (reads the weight field)
         "trial": nvox * (24 + 24 + 4 + 24 + 4 + 1 + 24 + 4 + 4),
         "cg_vec": nvox * 120,
     }.get(pass_name)
@@ -356,7 +362,8 @@ def run_gpu(args):
     peak, peak_kind = _peaks()
     achieved = bytes_launch / avg_s / 1e9
     traffic = _traffic(dom, n)
-    hv_only_ms = sum(stats[k][1] for k in ("xfwd_tangent", "y_fwd", "z_proj", "y_inv", "x_inv"))
+    hv_only_ms = sum(stats[k][1] for k in HV_PASSES)
+    hv_bytes = sum(_pass_bytes(n, k) for k in HV_PASSES)
     nprod = max(stats["z_proj"][0], 1)
 
     if rank != 0:
@@ -391,6 +398,10 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_launch},
+        "hv_roofline": {"bound": "hbm", "passes": list(HV_PASSES),
+                        "achieved": hv_bytes / (hv_only_ms / nprod / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": hv_bytes / (hv_only_ms / nprod / 1e3) / 1e9 / peak,
+                        "algorithmic_bytes_per_product": hv_bytes},
         "compulsory_fraction": {"bytes_per_voxel": 53, "frac": 53 * nvox / (hv_only_ms / nprod / 1e3) / 1e9 / peak},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 6 * nvox * 4,
@@ -596,8 +607,41 @@ def np_prod(d):
     return out
 
 
+def run_probe(args):
+    """Small untimed cases whose kernels an ncu capture can take in full."""
+    import numpy as np
+    import torch
+    from paper_2207_10657_gb300 import build as _build
+    _build.build()
+    if args.probe == "step":
+        from paper_2207_10657_gb300 import RVESolver
+        from synth import random_spheres
+        dims = (256, 256, 128)
+        pm = random_spheres(dims, count=100, rmin=4, rmax=10, seed=0)
+        s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, eta_eq=1e-6, eta_cg=1e-2, max_nr=50)
+        r = s.solve_step([0, 0, INC, 0, 0, 0], free_mask=FREE, raise_on_error=False)
+        torch.cuda.synchronize()
+        print("probe step", r["converged"], r["hv_products"], s.launch_count)
+        s.close()
+    else:
+        from paper_2207_10657_gb300.learned import SpectralOperator
+        net = SpectralOperator(layers=4, modes=16, seed=0)
+        rng = np.random.default_rng(0)
+        X = torch.from_numpy(rng.standard_normal((4, 64, 64, 64, 16)).astype(np.float32)).cuda()
+        T = torch.from_numpy(rng.standard_normal((4, 64, 64, 64, 6)).astype(np.float32)).cuda()
+        for _ in range(3):
+            net.loss_grad(X, T, (64, 64, 64))
+            net.adam_step(1e-3)
+        torch.cuda.synchronize()
+        print("probe fno", net.launch_count)
+        net.close()
+    return 0
+
+
 def main():
     args = _args()
+    if args.probe:
+        return run_probe(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch96":

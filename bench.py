@@ -90,10 +90,14 @@ def _peaks():
 
 
 def _kernel_hash():
+    """Hash of the sources of the single-cell solver path (the kernels whose
+    DRAM counters profiles/traffic.json holds); the network and the batched
+    solver live in files of their own and do not enter it."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2207_10657_gb300", "csrc")
+    skip = {"fno.cu", "batch.cu", "noalloc.cu"}
     for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh")):
+        if fn.endswith((".cu", ".cuh")) and fn not in skip:
             with open(os.path.join(csrc, fn), "rb") as f:
                 h.update(fn.encode())
                 h.update(f.read())
@@ -176,6 +180,19 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def reduce_over_ranks(dist, ms, count, device):
+    """Whole-job timing over the ranks of a replicas run: the slowest rank's
+    time (MAX) and the units all ranks processed (SUM).  dist None: one rank."""
+    if dist is None:
+        return float(ms), float(count)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    c = torch.tensor([float(count)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(c[0])
 
 
 # ------------------------------------------------------------ CPU oracle
@@ -312,15 +329,7 @@ def run_gpu(args):
     launches = s.launch_count - l0
     stats = binding.rve_pass_stats(s.h)
     binding.rve_pass_timing(s.h, False)
-    t_loc = torch.tensor([ms, float(hv)], dtype=torch.float64, device="cuda")
-    if dist:
-        tmax = t_loc.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        hsum = t_loc.clone()
-        dist.all_reduce(hsum[1:], op=dist.ReduceOp.SUM)
-        ms_max, hv_all = float(tmax[0]), float(hsum[1])
-    else:
-        ms_max, hv_all = ms, float(hv)
+    ms_max, hv_all = reduce_over_ranks(dist, ms, hv, "cuda")
     value = hv_all * nvox / (ms_max / 1e3)
 
     # ---------------- end to end through the public API with host buffers:
@@ -348,11 +357,8 @@ def run_gpu(args):
         st.synchronize()
     e2e_s = time.perf_counter() - t0
     hv_e = s.hv_count - hv_e0
-    e2e_val = hv_e * nvox / e2e_s
-    if dist:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_val = hv_e * nvox * ws / float(tt[0])
+    e2e_max, hv_e_all = reduce_over_ranks(dist, e2e_s, hv_e, "cuda")
+    e2e_val = hv_e_all * nvox / e2e_max
 
     # ---------------- roofline of the dominant pass
     dom = max((k for k in stats if stats[k][0] > 0), key=lambda k: stats[k][1])

@@ -261,7 +261,7 @@ def _pass_bytes(n, pass_name):
         "y_fwd": 2 * spec,
         "z_proj": 2 * spec,
         "y_inv": 2 * spec,
-        "x_inv": spec + 2 * field,  # with the fused CG dot product (reads the weight field)
+        "x_inv": spec + field,  # the CG curvature dot is formed in the x-forward pass
         "trial": nvox * (24 + 24 + 4 + 24 + 4 + 1 + 24 + 4 + 4),
         "cg_vec": nvox * 120,
     }.get(pass_name)

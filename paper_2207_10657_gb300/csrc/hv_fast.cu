@@ -35,11 +35,13 @@ template <int N, int NC, int MODE>
 __global__ void __launch_bounds__(kFT)
     kf_xfwd(const float* __restrict__ in, const uint8_t* __restrict__ phase, const float* __restrict__ dmg,
             const MatTable<float> mt, float2* __restrict__ spec, const long long nrows, const long long nvox,
-            const float2* __restrict__ tw) {
+            const float2* __restrict__ tw, double* __restrict__ partials) {
   constexpr int Q = xq<N, NC>();
   constexpr int NL = NC * Q / 2;
   constexpr int ND = NC == 6 ? 3 : 2;
   __shared__ __align__(16) float2 buf[NL * N];
+  __shared__ double red[32];
+  KSum<float> acc;  // in : (tangent : in), Mandel components (MODE 1 with partials)
   const long long row0 = (long long)blockIdx.x * Q;
   // one voxel per thread per step: consecutive threads take consecutive x,
   // so the line-interleaved shared-memory writes are (nearly) conflict free
@@ -64,8 +66,14 @@ __global__ void __launch_bounds__(kFT)
         float tr = 0.f;
 #pragma unroll
         for (int i = 0; i < ND; ++i) tr += v[b][i];
+        float dv = 0.f;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) v[b][c] = tmu * v[b][c] + (c < ND ? lam * tr : 0.f);
+        for (int c = 0; c < NC; ++c) {
+          const float sg = tmu * v[b][c] + (c < ND ? lam * tr : 0.f);
+          dv += v[b][c] * sg;
+          v[b][c] = sg;
+        }
+        if (partials) acc.add(dv);
       }
     }
 #pragma unroll
@@ -97,6 +105,11 @@ __global__ void __launch_bounds__(kFT)
       const long long row = row0 + q;
       if (row < nrows) spec[(c * nrows + row) * NXH + k] = h ? xb : xa;
     }
+  }
+  if (MODE == 1 && partials) {
+    double val[1] = {acc.value()};
+    block_sum<1>(val, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = val[0];
   }
 }
 
@@ -322,17 +335,21 @@ bool fast_size(int n) {
 
 template <int N>
 static cudaError_t xfwd_n(const GridDesc& g, const float* in, const uint8_t* phase, const float* dmg,
-                          const MatTable<float>& mt, float2* spec, const float2* tw, bool tangent, cudaStream_t st) {
+                          const MatTable<float>& mt, float2* spec, const float2* tw, bool tangent, double* partials,
+                          int* nblocks, cudaStream_t st) {
+  double* pd = tangent ? partials : nullptr;
   if (g.ncomp == 6) {
     constexpr int Q = xq<N, 6>();
     const int blocks = (int)((g.nrows + Q - 1) / Q);
-    if (tangent) kf_xfwd<N, 6, 1><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw);
-    else kf_xfwd<N, 6, 0><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw);
+    *nblocks = blocks;
+    if (tangent) kf_xfwd<N, 6, 1><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw, pd);
+    else kf_xfwd<N, 6, 0><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw, nullptr);
   } else {
     constexpr int Q = xq<N, 3>();
     const int blocks = (int)((g.nrows + Q - 1) / Q);
-    if (tangent) kf_xfwd<N, 3, 1><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw);
-    else kf_xfwd<N, 3, 0><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw);
+    *nblocks = blocks;
+    if (tangent) kf_xfwd<N, 3, 1><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw, pd);
+    else kf_xfwd<N, 3, 0><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw, nullptr);
   }
   return cudaGetLastError();
 }
@@ -391,9 +408,10 @@ static cudaError_t yproj2d_n(const GridDesc& g, float2* spec, const SpecWork<flo
 }
 
 cudaError_t fast_xfwd(const GridDesc& g, const float* in, const uint8_t* phase, const float* dmg,
-                      const MatTable<float>& mt, float2* spec, const float2* tw, bool tangent, cudaStream_t st) {
+                      const MatTable<float>& mt, float2* spec, const float2* tw, bool tangent, double* partials,
+                      int* nblocks, cudaStream_t st) {
 #define RVE_CASE(n_) \
-  if (g.nx == n_) return xfwd_n<n_>(g, in, phase, dmg, mt, spec, tw, tangent, st);
+  if (g.nx == n_) return xfwd_n<n_>(g, in, phase, dmg, mt, spec, tw, tangent, partials, nblocks, st);
   RVE_FAST_SIZES(RVE_CASE)
 #undef RVE_CASE
   return cudaErrorNotSupported;

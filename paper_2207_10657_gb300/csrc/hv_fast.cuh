@@ -8,8 +8,11 @@
 namespace rve {
 
 bool fast_size(int n);
+// With `partials` (tangent mode only) every block also writes its sum of
+// in : (tangent : in) to partials[block]; *nblocks receives the block count.
 cudaError_t fast_xfwd(const GridDesc& g, const float* in, const uint8_t* phase, const float* dmg,
-                      const MatTable<float>& mt, float2* spec, const float2* tw, bool tangent, cudaStream_t st);
+                      const MatTable<float>& mt, float2* spec, const float2* tw, bool tangent, double* partials,
+                      int* nblocks, cudaStream_t st);
 cudaError_t fast_xinv(const GridDesc& g, const float2* spec, float* out, const float* dotw, double* partials,
                       const float2* tw, bool dot, bool self, int* nblocks, cudaStream_t st);
 cudaError_t fast_ycols(const GridDesc& g, float2* spec, const float2* tw, bool inv, cudaStream_t st);

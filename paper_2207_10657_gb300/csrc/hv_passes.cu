@@ -113,8 +113,9 @@ cudaError_t spectral_setup(const GridDesc& g, SpecWork<R>& w) {
     const int e2 = std::min(kYThreads * kYEpt, (int)(kSmemCap / sizeof(C)));
     w.tz = std::max(1, std::min(pow2_floor(std::max(1, e2 / (3 * g.ny))), 64));
   }
-  w.max_partials = (int)((g.nrows + w.qx - 1) / w.qx) + 8;
-  w.max_partials = std::max(w.max_partials, 4096 * 8);
+  // one partial sum per x block: the compile-time x passes may take a
+  // single row per block (Nx = 512), so size for one per row
+  w.max_partials = (int)std::max<long long>(g.nrows + 8, 4096 * 8);
   if ((e = cudaMalloc(&w.partials, (size_t)w.max_partials * sizeof(double))) != cudaSuccess) return e;
   // opt in to large dynamic shared memory
   cudaFuncSetAttribute(k_xfwd<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
@@ -183,13 +184,22 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
   cudaError_t e;
   const int xblocks = (int)((g.nrows + w.qx - 1) / w.qx);
   const size_t xsm = (size_t)((g.ncomp * w.qx) / 2) * g.nx * sizeof(C);
+  // dot(in, G:B:in) for a compatible input (in = G:in, as every CG direction
+  // is) equals dot(in, B:in): the compiled x-forward pass forms it from the
+  // tangent it already computes, so the x-inverse need not read `in` again
+  bool fwd_dot = false;
+  int fwd_blocks = 0;
   // x forward (tangent fused)
   e = cudaErrorNotSupported;
   {
   PassScope ps(w.timer, st, PASS_XFWD);
   if constexpr (F32) {
-    if (fast_size(g.nx))
-      e = fast_xfwd(g, in, phase, damage, mt, w.spec, w.tw[0], mode == XIn::Tangent, st);
+    if (fast_size(g.nx)) {
+      const bool want = mode == XIn::Tangent && dot_with != nullptr && dot_with == in;
+      e = fast_xfwd(g, in, phase, damage, mt, w.spec, w.tw[0], mode == XIn::Tangent, want ? w.partials : nullptr,
+                    &fwd_blocks, st);
+      fwd_dot = want && e == cudaSuccess;
+    }
   }
   if (e == cudaErrorNotSupported) {
     if (mode == XIn::Tangent)
@@ -241,7 +251,7 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
     ++nl;
   }
   const R scale = (R)(1.0 / (double)g.nvox);
-  const bool dot = dot_with != nullptr;
+  const bool dot = dot_with != nullptr && !fwd_dot;
   const bool self = dot && (dot_with == out);
   int nblocks = xblocks;
   e = cudaErrorNotSupported;
@@ -264,8 +274,8 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
   }
   if (e != cudaSuccess) return e;
   ++nl;
-  if (dot) {
-    e = reduce_partials(w.partials, nblocks, 1, dot_out, st, &nl);
+  if (dot || fwd_dot) {
+    e = reduce_partials(w.partials, fwd_dot ? fwd_blocks : nblocks, 1, dot_out, st, &nl);
     if (e != cudaSuccess) return e;
   }
   if (nlaunch) *nlaunch += nl;

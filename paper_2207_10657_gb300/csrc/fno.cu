@@ -46,6 +46,7 @@ struct GemmArgs {
   long long ldc, sC;
   float alpha, beta;
   int batch, ksplit, kchunk;  // ksplit > 1: K is cut in chunks whose products are added atomically into C
+  int vecA, vecB;              // operand rows and batch strides are 16-byte aligned: float4 staging
 };
 
 constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
@@ -83,25 +84,102 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
     for (int k0 = kbeg; k0 < kend; k0 += GBK) {
-      for (int e = threadIdx.x; e < GBM * GBK; e += 128) {
-        int mm, kk;
-        if (TA) { mm = e % GBM; kk = e / GBM; }  // consecutive threads: consecutive m (contiguous)
-        else { kk = e % GBK; mm = e / GBK; }
-        const int gm = m0 + mm, gk = k0 + kk;
-        float v = 0.f;
-        if (gm < g.M && gk < kend)
-          v = ldf<TA_T>(A, TA ? (long long)gk * g.lda + gm : (long long)gm * g.lda + gk);
-        As[mm][kk] = __float2bfloat16(v);
+      // Stage the A and B tiles as BF16.  With aligned operands every
+      // thread moves 4 consecutive elements of the contiguous dimension per
+      // float4 load; ragged edges fall back to guarded scalar loads.
+      if (g.vecA) {
+        constexpr int CH = GBM * GBK / 4;
+        for (int e = threadIdx.x; e < CH; e += 128) {
+          float v[4];
+          if (TA) {  // contiguous along m
+            const int kk = e / (GBM / 4), mm = 4 * (e % (GBM / 4));
+            const int gm = m0 + mm, gk = k0 + kk;
+            if (gk < kend && gm + 3 < g.M) {
+              const float4 q = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(A) + (long long)gk * g.lda + gm);
+              v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+            } else {
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                v[i] = (gk < kend && gm + i < g.M) ? ldf<TA_T>(A, (long long)gk * g.lda + gm + i) : 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) As[mm + i][kk] = __float2bfloat16(v[i]);
+          } else {  // contiguous along k
+            const int mm = e / (GBK / 4), kk = 4 * (e % (GBK / 4));
+            const int gm = m0 + mm, gk = k0 + kk;
+            if (gm < g.M && gk + 3 < kend) {
+              const float4 q = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(A) + (long long)gm * g.lda + gk);
+              v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+            } else {
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                v[i] = (gm < g.M && gk + i < kend) ? ldf<TA_T>(A, (long long)gm * g.lda + gk + i) : 0.f;
+            }
+            __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]), hi = __floats2bfloat162_rn(v[2], v[3]);
+            uint2 w;
+            w.x = *reinterpret_cast<uint32_t*>(&lo);
+            w.y = *reinterpret_cast<uint32_t*>(&hi);
+            *reinterpret_cast<uint2*>(&As[mm][kk]) = w;
+          }
+        }
+      } else {
+        for (int e = threadIdx.x; e < GBM * GBK; e += 128) {
+          int mm, kk;
+          if (TA) { mm = e % GBM; kk = e / GBM; }  // consecutive threads: consecutive m (contiguous)
+          else { kk = e % GBK; mm = e / GBK; }
+          const int gm = m0 + mm, gk = k0 + kk;
+          float v = 0.f;
+          if (gm < g.M && gk < kend)
+            v = ldf<TA_T>(A, TA ? (long long)gk * g.lda + gm : (long long)gm * g.lda + gk);
+          As[mm][kk] = __float2bfloat16(v);
+        }
       }
-      for (int e = threadIdx.x; e < GBN * GBK; e += 128) {
-        int nn, kk;
-        if (TB) { kk = e % GBK; nn = e / GBK; }
-        else { nn = e % GBN; kk = e / GBN; }
-        const int gn = n0 + nn, gk = k0 + kk;
-        float v = 0.f;
-        if (gn < g.N && gk < kend)
-          v = ldf<TB_T>(B, TB ? (long long)gn * g.ldb + gk : (long long)gk * g.ldb + gn);
-        Bs[nn][kk] = __float2bfloat16(v);
+      if (g.vecB) {
+        constexpr int CH = GBN * GBK / 4;
+        for (int e = threadIdx.x; e < CH; e += 128) {
+          float v[4];
+          if (TB) {  // contiguous along k
+            const int nn = e / (GBK / 4), kk = 4 * (e % (GBK / 4));
+            const int gn = n0 + nn, gk = k0 + kk;
+            if (gn < g.N && gk + 3 < kend) {
+              const float4 q = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(B) + (long long)gn * g.ldb + gk);
+              v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+            } else {
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                v[i] = (gn < g.N && gk + i < kend) ? ldf<TB_T>(B, (long long)gn * g.ldb + gk + i) : 0.f;
+            }
+            __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]), hi = __floats2bfloat162_rn(v[2], v[3]);
+            uint2 w;
+            w.x = *reinterpret_cast<uint32_t*>(&lo);
+            w.y = *reinterpret_cast<uint32_t*>(&hi);
+            *reinterpret_cast<uint2*>(&Bs[nn][kk]) = w;
+          } else {  // contiguous along n
+            const int kk = e / (GBN / 4), nn = 4 * (e % (GBN / 4));
+            const int gn = n0 + nn, gk = k0 + kk;
+            if (gk < kend && gn + 3 < g.N) {
+              const float4 q = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(B) + (long long)gk * g.ldb + gn);
+              v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+            } else {
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                v[i] = (gk < kend && gn + i < g.N) ? ldf<TB_T>(B, (long long)gk * g.ldb + gn + i) : 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) Bs[nn + i][kk] = __float2bfloat16(v[i]);
+          }
+        }
+      } else {
+        for (int e = threadIdx.x; e < GBN * GBK; e += 128) {
+          int nn, kk;
+          if (TB) { kk = e % GBK; nn = e / GBK; }
+          else { nn = e % GBN; kk = e / GBN; }
+          const int gn = n0 + nn, gk = k0 + kk;
+          float v = 0.f;
+          if (gn < g.N && gk < kend)
+            v = ldf<TB_T>(B, TB ? (long long)gn * g.ldb + gk : (long long)gk * g.ldb + gn);
+          Bs[nn][kk] = __float2bfloat16(v);
+        }
       }
       __syncthreads();
 #pragma unroll
@@ -457,7 +535,11 @@ cudaError_t gemm(rve_fno_ctx* c, bool ta, bool tb, int M, int N, int K, const TA
     if (e != cudaSuccess) return e;
   }
   const int kchunk = ((K + ksplit - 1) / ksplit + GBK - 1) / GBK * GBK;
-  GemmArgs g{M, N, K, A, lda, sA, B, ldb, sB, Cm, ldc, sC, alpha, beta, batch, ksplit, kchunk};
+  auto al16 = [](const void* p, long long ld, long long st) {
+    return ((reinterpret_cast<uintptr_t>(p) & 15) == 0 && ld % 4 == 0 && st % 4 == 0) ? 1 : 0;
+  };
+  GemmArgs g{M, N, K, A, lda, sA, B, ldb, sB, Cm, ldc, sC, alpha, beta, batch, ksplit, kchunk,
+             al16(A, lda, sA), al16(B, ldb, sB)};
   const int zdim = (int)std::min<long long>((long long)batch * ksplit, 65535);
   dim3 grid((M + GBM - 1) / GBM, (N + GBN - 1) / GBN, zdim);
   if (ta && tb) k_gemm<TA_T, TB_T, true, true><<<grid, 128, 0, c->st>>>(g);

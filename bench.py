@@ -468,6 +468,7 @@ def run_batch(args):
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
         b = RVEBatch(dims, pms, [MATRIX, STIFF], stream=st, eta_eq=1e-6, eta_cg=1e-2, max_nr=args.batch_max_nr)
+        tuned = b.autotune(reps=3)
 
     def step():
         b.reset()
@@ -528,7 +529,8 @@ def run_batch(args):
                    "hv_per_member_mean": sum(r["hv_products"] for r in reps) / len(reps),
                    "sequential_single_contexts_ms": t_single * 1e3,
                    "sequential_single_contexts_voxel_hv_per_s": hv_single / t_single,
-                   "batched_speedup": (t_single * 1e3) / (ms / args.steps)},
+                   "batched_speedup": (t_single * 1e3) / (ms / args.steps),
+                   "autotune": tuned},
         "gpu_launches": launches, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

@@ -230,6 +230,20 @@ rve_status rve_batch_get_state(rve_batch_t, int i, float* strain_dev, float* kap
 /* Back to the unloaded state (eps = 0, kappa_n = 0) for every member; the
  * trust radii are kept. */
 rve_status rve_batch_reset(rve_batch_t);
+/* Schedule autotuner of the batched spectral passes (not part of the
+ * method): times one batched Hessian-vector product of every member for a
+ * few schedules -- each member's x / y / z tile divided by 1, 2 or 4, and
+ * every axis's radix order natural or reversed -- `reps` times each (1..1000),
+ * by coordinate search (a candidate must be 2 % faster), and keeps the
+ * fastest for all later calls.  base_ms_host / best_ms_host (may be NULL):
+ * time per product of the default schedule and of the chosen one;
+ * schedule_host (may be NULL, 4 ints): x, y, z divisors and 1 if the radix
+ * order is reversed.  Overwrites the CG scratch vectors, so call it between
+ * load steps; synchronises the stream. */
+rve_status rve_batch_autotune(rve_batch_t, int reps, double* base_ms_host, double* best_ms_host,
+                              int* schedule_host);
+/* Install one schedule by hand (4 ints as above; divisors 1, 2 or 4). */
+rve_status rve_batch_set_schedule(rve_batch_t, const int* schedule_host);
 const char* rve_batch_last_error(rve_batch_t);
 long long rve_batch_hv_count(rve_batch_t);
 long long rve_batch_launch_count(rve_batch_t);

@@ -77,6 +77,9 @@ _SIGS = [
     ("rve_batch_get_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p]),
     ("rve_batch_reset", ctypes.c_int, [ctypes.c_void_p]),
+    ("rve_batch_set_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    ("rve_batch_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     ("rve_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("rve_batch_hv_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("rve_batch_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
@@ -276,6 +279,18 @@ def rve_batch_get_state(h, i, strain_ptr=0, kappa_ptr=0, stress_ptr=0, damage_pt
 
 def rve_batch_reset(h):
     _bcheck(lib().rve_batch_reset(h), h)
+
+
+def rve_batch_set_schedule(h, schedule):
+    _bcheck(lib().rve_batch_set_schedule(h, (ctypes.c_int * 4)(*schedule)), h)
+
+
+def rve_batch_autotune(h, reps=3):
+    """Pick the fastest batched-pass schedule; returns (default ms, chosen ms, schedule) per product."""
+    base, ms = ctypes.c_double(), ctypes.c_double()
+    sched = (ctypes.c_int * 4)()
+    _bcheck(lib().rve_batch_autotune(h, reps, ctypes.byref(base), ctypes.byref(ms), sched), h)
+    return base.value, ms.value, list(sched)
 
 
 def rve_batch_hv_count(h):

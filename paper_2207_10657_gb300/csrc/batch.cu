@@ -471,6 +471,8 @@ struct rve_batch_ctx {
   bool any3d = false, any2d = false;
   cudaGraphExec_t g_iter = nullptr, g_dir = nullptr;
   cudaStream_t cap = nullptr;  // private stream the graphs are captured on (launched on st)
+  int part_items = 0;           // capacity of `part` in work items (12 doubles each)
+  int sched[4] = {1, 1, 1, 0};  // schedule: x / y / z tile divisors, reversed radix order
   long long launches = 0, hv = 0;
   std::string err = "no error";
 };
@@ -980,6 +982,7 @@ rve_status batch_init(rve_batch_ctx* c, const int* dims, const int* ndims, const
   BCK(cudaMalloc(&c->dR, 2 * n * sizeof(double)), "radii");
   const int maxitems = std::max({c->total[BP_X], c->total[BP_VEC], c->total[BP_VOX]});
   BCK(cudaMalloc(&c->part, (size_t)maxitems * 12 * sizeof(double)), "partials");
+  c->part_items = maxitems;
   BCK(cudaMemsetAsync(c->eps, 0, fb, c->st), "memset");
   BCK(cudaMemsetAsync(c->khist, 0, vb, c->st), "memset");
   BCK(cudaMemsetAsync(c->kap, 0, vb, c->st), "memset");
@@ -998,6 +1001,101 @@ rve_status batch_init(rve_batch_ctx* c, const int* dims, const int* ndims, const
   BCK(reset_counters(c), "memset");
   BCK(trial(c, gate_bits(all), nullptr, false), "initial state");
   BCK(cudaStreamSynchronize(c->st), "synchronize");
+  return RVE_OK;
+}
+
+// ---------------------------------------------------------------- autotune
+// A schedule of the batched spectral passes: every member's x / y / z tile
+// (rows per x item, kx columns per y item and per z item) divided by
+// sx / sy / sz (the tiles of spectral_setup are the largest the per-thread
+// element budgets allow, so only smaller ones are candidates), and the
+// radix order of every axis plan natural or reversed (any order is a valid
+// Stockham factorisation).  Work-item counts, dynamic shared memory, the
+// partial-sum buffer and the device descriptors follow; captured graphs are
+// dropped so that they are recaptured with the new schedule.
+void reverse_plan(AxisPlan& p) {
+  for (int a = 0, b = p.nstages - 1; a < b; ++a, --b) std::swap(p.radix[a], p.radix[b]);
+}
+
+rve_status apply_schedule(rve_batch_ctx* c, const int sched[4]) {
+  const int n = c->n;
+  const int passes[4] = {BP_X, BP_Y, BP_Z, BP_2D};
+  for (int p : passes) c->smem[p] = 0;
+  for (int i = 0; i < n; ++i) {
+    const GridDesc& g = c->g[i];
+    const SpecWork<R>& w = c->sw[i];
+    BDesc& d = c->desc[i];
+    int qx = std::max(1, w.qx / sched[0]);
+    if (g.ncomp & 1) qx = std::max(2, qx & ~1);
+    d.qx = qx;
+    d.ty = std::max(1, w.ty / sched[1]);
+    d.tz = std::max(1, w.tz / sched[2]);
+    d.px = w.px;
+    d.py = w.py;
+    d.pz = w.pz;
+    if (sched[3]) {
+      reverse_plan(d.px);
+      reverse_plan(d.py);
+      reverse_plan(d.pz);
+    }
+    const int nb[4] = {
+        (int)((g.nrows + d.qx - 1) / d.qx),
+        g.ndim == 3 ? ((g.nxh + d.ty - 1) / d.ty) * g.nz * g.ncomp : 0,
+        g.ndim == 3 ? ((g.nxh + d.tz - 1) / d.tz) * g.ny : 0,
+        g.ndim == 2 ? (g.nxh + d.tz - 1) / d.tz : 0,
+    };
+    for (int k = 0; k < 4; ++k) c->hstart[passes[k]][i + 1] = c->hstart[passes[k]][i] + nb[k];
+    c->smem[BP_X] = std::max(c->smem[BP_X], (size_t)((g.ncomp * d.qx) / 2) * g.nx * sizeof(C));
+    if (g.ndim == 3) {
+      c->smem[BP_Y] = std::max(c->smem[BP_Y], (size_t)d.ty * g.ny * sizeof(C));
+      c->smem[BP_Z] = std::max(c->smem[BP_Z], (size_t)6 * d.tz * g.nz * sizeof(C));
+    } else {
+      c->smem[BP_2D] = std::max(c->smem[BP_2D], (size_t)3 * d.tz * g.ny * sizeof(C));
+    }
+  }
+  std::vector<int> nbh((size_t)BP_N * n);
+  for (int p = 0; p < BP_N; ++p) {
+    c->total[p] = c->hstart[p][n];
+    for (int i = 0; i < n; ++i) nbh[(size_t)p * n + i] = c->hstart[p][i + 1] - c->hstart[p][i];
+  }
+  BCK(cudaStreamSynchronize(c->st), "synchronize");
+  BCK(cudaMemcpy(c->dnb, nbh.data(), nbh.size() * sizeof(int), cudaMemcpyHostToDevice), "schedule");
+  BCK(cudaMemcpy(c->dD, c->desc.data(), n * sizeof(BDesc), cudaMemcpyHostToDevice), "descriptors");
+  const int maxitems = std::max({c->total[BP_X], c->total[BP_VEC], c->total[BP_VOX]});
+  if (maxitems > c->part_items) {
+    BCK(cudaFree(c->part), "partials");
+    c->part = nullptr;
+    BCK(cudaMalloc(&c->part, (size_t)maxitems * 12 * sizeof(double)), "partials");
+    c->part_items = maxitems;
+  }
+  if (c->g_iter) cudaGraphExecDestroy(c->g_iter);
+  if (c->g_dir) cudaGraphExecDestroy(c->g_dir);
+  c->g_iter = c->g_dir = nullptr;
+  for (int k = 0; k < 4; ++k) c->sched[k] = sched[k];
+  return RVE_OK;
+}
+
+// mean time of one batched Hessian-vector product of every member (ms)
+rve_status time_products(rve_batch_ctx* c, int reps, double* ms) {
+  std::vector<char> all(c->n, 1);
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0), "event");
+  BCK(cudaEventCreate(&e1), "event");
+  cudaError_t e = cudaSuccess;
+  // one untimed product (first use of the schedule), then `reps` timed
+  for (int k = 0; k <= reps && e == cudaSuccess; ++k) {
+    if (k == 1) e = cudaEventRecord(e0, c->st);
+    if (e == cudaSuccess) e = reset_counters(c);
+    if (e == cudaSuccess) e = batch_apply(c, c->d, c->Hd, true, nullptr, 0, gate_bits(all));
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  BCK(e, "timed products");
+  *ms = (double)t / reps;
   return RVE_OK;
 }
 
@@ -1078,6 +1176,52 @@ rve_status rve_batch_hessp(rve_batch_t c, const float* const* v_dev, float* cons
     const size_t b = (size_t)c->g[i].ncomp * c->g[i].nvox * sizeof(R);
     BCK(cudaMemcpyAsync(out_dev[i], c->Hd + c->desc[i].foff, b, cudaMemcpyDeviceToDevice, c->st), "output copy");
   }
+  return RVE_OK;
+}
+
+rve_status rve_batch_set_schedule(rve_batch_t c, const int* schedule_host) {
+  if (!c) return RVE_ERR_ARG;
+  if (!schedule_host) return bfail(c, RVE_ERR_ARG, "NULL schedule");
+  for (int k = 0; k < 3; ++k)
+    if (schedule_host[k] != 1 && schedule_host[k] != 2 && schedule_host[k] != 4)
+      return bfail(c, RVE_ERR_ARG, "tile divisors must be 1, 2 or 4");
+  if (schedule_host[3] != 0 && schedule_host[3] != 1) return bfail(c, RVE_ERR_ARG, "radix order flag must be 0 or 1");
+  return apply_schedule(c, schedule_host);
+}
+
+rve_status rve_batch_autotune(rve_batch_t c, int reps, double* base_ms_host, double* best_ms_host,
+                              int* schedule_host) {
+  if (!c) return RVE_ERR_ARG;
+  if (reps < 1 || reps > 1000) return bfail(c, RVE_ERR_ARG, "reps must be in [1, 1000]");
+  // the CG scratch vectors d (zeroed) and Hd carry the timed products
+  BCK(cudaMemsetAsync(c->d, 0, (size_t)c->nfield * sizeof(R), c->st), "memset");
+  int best[4] = {1, 1, 1, 0};
+  rve_status s = apply_schedule(c, best);
+  if (s != RVE_OK) return s;
+  double tbest = 0;
+  if ((s = time_products(c, reps, &tbest)) != RVE_OK) return s;
+  if (base_ms_host) *base_ms_host = tbest;
+  // coordinate search: tile divisors 2 and 4 per pass, then the radix order;
+  // a candidate must beat the incumbent by 2 % to replace it
+  for (int axis = 0; axis < 4; ++axis) {
+    const int cands[2] = {axis < 3 ? 2 : 1, axis < 3 ? 4 : 0};
+    for (int v : cands) {
+      if (axis == 3 && v == 0) continue;
+      int cand[4] = {best[0], best[1], best[2], best[3]};
+      cand[axis] = v;
+      if ((s = apply_schedule(c, cand)) != RVE_OK) return s;
+      double t = 0;
+      if ((s = time_products(c, reps, &t)) != RVE_OK) return s;
+      if (t < 0.98 * tbest) {
+        tbest = t;
+        for (int k = 0; k < 4; ++k) best[k] = cand[k];
+      }
+    }
+  }
+  if ((s = apply_schedule(c, best)) != RVE_OK) return s;
+  if (best_ms_host) *best_ms_host = tbest;
+  if (schedule_host)
+    for (int k = 0; k < 4; ++k) schedule_host[k] = best[k];
   return RVE_OK;
 }
 

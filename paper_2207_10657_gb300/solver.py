@@ -189,6 +189,15 @@ class RVEBatch:
     def reset(self):
         B.rve_batch_reset(self.h)
 
+    def autotune(self, reps=3):
+        """Choose the fastest tile / radix-order schedule of the batched
+        passes by timing; returns {"ms_per_product", "ms_per_product_default",
+        "schedule"}."""
+        base, ms, sched = B.rve_batch_autotune(self.h, reps)
+        return {"ms_per_product": ms, "ms_per_product_default": base,
+                "schedule": {"x_div": sched[0], "y_div": sched[1], "z_div": sched[2],
+                             "radix_reversed": bool(sched[3])}}
+
     def solve_step(self, dE_list, free_masks=None, raise_on_error=True):
         st, reps = B.rve_batch_solve_step(self.h, dE_list, free_masks, raise_on_error)
         out = [_report_dict(r) for r in reps]

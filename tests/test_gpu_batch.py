@@ -51,6 +51,39 @@ def test_batched_hessp_matches_single_and_oracle():
     b.close()
 
 
+def test_every_schedule_gives_the_same_products():
+    """Every schedule the autotuner may pick (tile divisors 1, 2, 4 per pass,
+    natural or reversed radix order) gives the same batched Hv as the single
+    contexts; the tuned schedule is kept for later calls."""
+    from paper_2207_10657_gb300 import RVEBatch, RVESolver, binding as B, build
+    build.build()
+    dims = [(64, 64), (96, 60), (32, 32, 32), (48, 40, 30), (16, 24, 20)]
+    pms = [_micro(d, 60 + i) for i, d in enumerate(dims)]
+    vs = [random_field(3 if len(d) == 2 else 6, d, seed=70 + i, dtype=np.float32) for i, d in enumerate(dims)]
+    refs = []
+    for i, d in enumerate(dims):
+        s = RVESolver(d, pms[i], [MATRIX, STIFF], precision=32)
+        refs.append(s.hessp(torch.from_numpy(vs[i]).cuda()).cpu().numpy())
+        s.close()
+    b = RVEBatch(dims, pms, [MATRIX, STIFF])
+    for sx in (1, 2, 4):
+        for sy in (1, 2, 4):
+            for sz in (1, 2, 4):
+                for rev in (0, 1):
+                    B.rve_batch_set_schedule(b.h, [sx, sy, sz, rev])
+                    outs = b.hessp([torch.from_numpy(v).cuda() for v in vs])
+                    for i in range(len(dims)):
+                        assert _rel(outs[i].cpu().numpy(), refs[i]) < 2e-6, (dims[i], sx, sy, sz, rev)
+    with pytest.raises(B.RveError):
+        B.rve_batch_set_schedule(b.h, [3, 1, 1, 0])
+    tuned = b.autotune(reps=2)
+    assert tuned["ms_per_product"] > 0 and tuned["ms_per_product"] <= tuned["ms_per_product_default"]
+    outs = b.hessp([torch.from_numpy(v).cuda() for v in vs])
+    for i in range(len(dims)):
+        assert _rel(outs[i].cpu().numpy(), refs[i]) < 2e-6, (dims[i], tuned)
+    b.close()
+
+
 def test_batched_load_steps_match_single_contexts():
     """Two load increments (elastic, then the onset of damage) per member,
     each member with its own load direction: the batched lockstep solve

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kFT)
   constexpr int ND = NC == 6 ? 3 : 2;
   __shared__ __align__(16) float2 buf[NL * N];
   __shared__ double red[32];
-  KSum<float> acc;  // in : (tangent : in), Mandel components (MODE 1 with partials)
+  float acc = 0.f;  // in : (tangent : in) over this thread's few voxels (MODE 1 with partials)
   const long long row0 = (long long)blockIdx.x * Q;
   // one voxel per thread per step: consecutive threads take consecutive x,
   // so the line-interleaved shared-memory writes are (nearly) conflict free
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kFT)
           dv += v[b][c] * sg;
           v[b][c] = sg;
         }
-        if (partials) acc.add(dv);
+        acc += dv;
       }
     }
 #pragma unroll
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kFT)
     }
   }
   if (MODE == 1 && partials) {
-    double val[1] = {acc.value()};
+    double val[1] = {(double)acc};
     block_sum<1>(val, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = val[0];
   }

@@ -114,11 +114,19 @@ __global__ void __launch_bounds__(kFT)
 }
 
 // ------------------------------------------------------------ x inverse
-template <int N, int NC, bool DOT>
+// CG: instead of storing the product Hd, apply the CG iterate / residual
+// update of Algorithm 1 with it (status, alpha and tau read from the device
+// scalars): running, z += alpha d and r += alpha Hd with the sums r'.r',
+// r'.r and z'.z per block in partials[3 b + s]; on a boundary or
+// negative-curvature exit, z += tau d.
+template <int N, int NC, bool DOT, bool CG = false>
 __global__ void __launch_bounds__(kFT)
     kf_xinv(const float2* __restrict__ spec, float* __restrict__ out, const float* __restrict__ dotw,
             double* __restrict__ partials, const long long nrows, const long long nvox,
-            const float2* __restrict__ tw, const float scale, const bool self_dot) {
+            const float2* __restrict__ tw, const float scale, const bool self_dot, float* __restrict__ cz = nullptr,
+            float* __restrict__ cr = nullptr, const float* __restrict__ cd = nullptr,
+            const int* __restrict__ cstatus = nullptr, const double* __restrict__ calpha = nullptr,
+            const double* __restrict__ ctau = nullptr) {
   constexpr int Q = xq<N, NC>();
   constexpr int NL = NC * Q / 2;
   constexpr int NXH = N / 2 + 1;
@@ -163,6 +171,53 @@ __global__ void __launch_bounds__(kFT)
   }
   __syncthreads();
   fft_ct<N, NL, kFT, true>(buf, tw);
+  if constexpr (CG) {
+    const int status = *cstatus;
+    const bool run = status == 0, exit_tau = status == 2 || status == 3;  // running / boundary, negative curvature
+    const float al = (float)*calpha, ta = (float)*ctau;
+    KSum<float> cs[3];
+    constexpr int SITEMS = Q * NC * N;
+    constexpr int SSTEPS = (SITEMS + kFT - 1) / kFT;
+    constexpr int SB = SSTEPS < 4 ? SSTEPS : 4;
+    for (int s0 = 0; s0 < SSTEPS; s0 += SB) {
+      float o[SB], zv[SB], rv[SB], dv[SB];
+      long long off[SB];
+      bool ok[SB];
+#pragma unroll
+      for (int b = 0; b < SB; ++b) {
+        const int idx = threadIdx.x + (s0 + b) * kFT;
+        const int rho = idx / N, x = idx - (idx / N) * N;
+        const int q = rho / NC, c = rho - (rho / NC) * NC;
+        const long long row = row0 + q;
+        ok[b] = (s0 + b < SSTEPS) && idx < SITEMS && row < nrows && (run || exit_tau);
+        off[b] = c * nvox + row * N + x;
+        o[b] = ok[b] ? reinterpret_cast<const float*>(&buf[x * NL + (rho >> 1)])[rho & 1] * scale : 0.f;
+        zv[b] = ok[b] ? cz[off[b]] : 0.f;
+        dv[b] = ok[b] ? __ldg(cd + off[b]) : 0.f;
+        rv[b] = (ok[b] && run) ? cr[off[b]] : 0.f;
+      }
+#pragma unroll
+      for (int b = 0; b < SB; ++b) {
+        if (!ok[b]) continue;
+        if (run) {
+          const float zn = zv[b] + al * dv[b], rn = rv[b] + al * o[b];
+          cz[off[b]] = zn;
+          cr[off[b]] = rn;
+          cs[0].add(rn * rn);
+          cs[1].add(rn * rv[b]);
+          cs[2].add(zn * zn);
+        } else {
+          cz[off[b]] = zv[b] + ta * dv[b];
+        }
+      }
+    }
+    __shared__ double red3[3 * 32];
+    double v3[3] = {cs[0].value(), cs[1].value(), cs[2].value()};
+    block_sum<3>(v3, red3);
+    if (threadIdx.x == 0)
+      for (int k = 0; k < 3; ++k) partials[3 * (long long)blockIdx.x + k] = v3[k];
+    return;
+  }
   KSum<float> acc;
   constexpr int SITEMS = Q * NC * N;
   constexpr int SSTEPS = (SITEMS + kFT - 1) / kFT;
@@ -421,6 +476,37 @@ cudaError_t fast_xinv(const GridDesc& g, const float2* spec, float* out, const f
                       const float2* tw, bool dot, bool self, int* nblocks, cudaStream_t st) {
 #define RVE_CASE(n_) \
   if (g.nx == n_) return xinv_n<n_>(g, spec, out, dotw, partials, tw, dot, self, nblocks, st);
+  RVE_FAST_SIZES(RVE_CASE)
+#undef RVE_CASE
+  return cudaErrorNotSupported;
+}
+
+template <int N>
+static cudaError_t xinv_cg_n(const GridDesc& g, const float2* spec, float* z, float* r, const float* d,
+                             const int* status, const double* alpha, const double* tau, double* partials,
+                             const float2* tw, int* nblocks, cudaStream_t st) {
+  const float scale = (float)(1.0 / (double)g.nvox);
+  if (g.ncomp == 6) {
+    constexpr int Q = xq<N, 6>();
+    const int blocks = (int)((g.nrows + Q - 1) / Q);
+    *nblocks = blocks;
+    kf_xinv<N, 6, false, true><<<blocks, kFT, 0, st>>>(spec, nullptr, nullptr, partials, g.nrows, g.nvox, tw, scale,
+                                                       false, z, r, d, status, alpha, tau);
+  } else {
+    constexpr int Q = xq<N, 3>();
+    const int blocks = (int)((g.nrows + Q - 1) / Q);
+    *nblocks = blocks;
+    kf_xinv<N, 3, false, true><<<blocks, kFT, 0, st>>>(spec, nullptr, nullptr, partials, g.nrows, g.nvox, tw, scale,
+                                                       false, z, r, d, status, alpha, tau);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t fast_xinv_cg(const GridDesc& g, const float2* spec, float* z, float* r, const float* d, const int* status,
+                         const double* alpha, const double* tau, double* partials, const float2* tw, int* nblocks,
+                         cudaStream_t st) {
+#define RVE_CASE(n_) \
+  if (g.nx == n_) return xinv_cg_n<n_>(g, spec, z, r, d, status, alpha, tau, partials, tw, nblocks, st);
   RVE_FAST_SIZES(RVE_CASE)
 #undef RVE_CASE
   return cudaErrorNotSupported;

@@ -15,6 +15,12 @@ cudaError_t fast_xfwd(const GridDesc& g, const float* in, const uint8_t* phase, 
                       int* nblocks, cudaStream_t st);
 cudaError_t fast_xinv(const GridDesc& g, const float2* spec, float* out, const float* dotw, double* partials,
                       const float2* tw, bool dot, bool self, int* nblocks, cudaStream_t st);
+// x-inverse that applies the Steihaug-CG iterate / residual update with the
+// product instead of storing it (status / alpha / tau: device scalars;
+// partials: three sums per block, block-major).
+cudaError_t fast_xinv_cg(const GridDesc& g, const float2* spec, float* z, float* r, const float* d, const int* status,
+                         const double* alpha, const double* tau, double* partials, const float2* tw, int* nblocks,
+                         cudaStream_t st);
 cudaError_t fast_ycols(const GridDesc& g, float2* spec, const float2* tw, bool inv, cudaStream_t st);
 cudaError_t fast_zproj(const GridDesc& g, float2* spec, const SpecWork<float>& w, cudaStream_t st);
 cudaError_t fast_yproj2d(const GridDesc& g, float2* spec, const SpecWork<float>& w, cudaStream_t st);

@@ -113,9 +113,9 @@ cudaError_t spectral_setup(const GridDesc& g, SpecWork<R>& w) {
     const int e2 = std::min(kYThreads * kYEpt, (int)(kSmemCap / sizeof(C)));
     w.tz = std::max(1, std::min(pow2_floor(std::max(1, e2 / (3 * g.ny))), 64));
   }
-  // one partial sum per x block: the compile-time x passes may take a
-  // single row per block (Nx = 512), so size for one per row
-  w.max_partials = (int)std::max<long long>(g.nrows + 8, 4096 * 8);
+  // up to three partial sums per x block (the fused CG x-inverse), and the
+  // compile-time x passes may take a single row per block (Nx = 512)
+  w.max_partials = (int)std::max<long long>(3 * g.nrows + 8, 4096 * 8);
   if ((e = cudaMalloc(&w.partials, (size_t)w.max_partials * sizeof(double))) != cudaSuccess) return e;
   // opt in to large dynamic shared memory
   cudaFuncSetAttribute(k_xfwd<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
@@ -174,43 +174,14 @@ void spectral_free(SpecWork<R>& w) {
   w.partials = nullptr;
 }
 
+// y / z passes with the projection (3D) or the y pass with the projection
+// (2D), between the x-forward and the x-inverse passes.
 template <typename R>
-cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>& mt, const R* in,
-                           const uint8_t* phase, const R* damage, XIn mode, R* out,
-                           const R* dot_with, double* dot_out, cudaStream_t st, long long* nlaunch) {
+static cudaError_t spectral_middle(const GridDesc& g, SpecWork<R>& w, cudaStream_t st, long long* nlp) {
   using C = Cx<R>;
   constexpr bool F32 = std::is_same<R, float>::value;
   long long nl = 0;
   cudaError_t e;
-  const int xblocks = (int)((g.nrows + w.qx - 1) / w.qx);
-  const size_t xsm = (size_t)((g.ncomp * w.qx) / 2) * g.nx * sizeof(C);
-  // dot(in, G:B:in) for a compatible input (in = G:in, as every CG direction
-  // is) equals dot(in, B:in): the compiled x-forward pass forms it from the
-  // tangent it already computes, so the x-inverse need not read `in` again
-  bool fwd_dot = false;
-  int fwd_blocks = 0;
-  // x forward (tangent fused)
-  e = cudaErrorNotSupported;
-  {
-  PassScope ps(w.timer, st, PASS_XFWD);
-  if constexpr (F32) {
-    if (fast_size(g.nx)) {
-      const bool want = mode == XIn::Tangent && dot_with != nullptr && dot_with == in;
-      e = fast_xfwd(g, in, phase, damage, mt, w.spec, w.tw[0], mode == XIn::Tangent, want ? w.partials : nullptr,
-                    &fwd_blocks, st);
-      fwd_dot = want && e == cudaSuccess;
-    }
-  }
-  if (e == cudaErrorNotSupported) {
-    if (mode == XIn::Tangent)
-      k_xfwd<R, 1><<<xblocks, kXThreads, xsm, st>>>(in, phase, damage, mt, w.spec, g, w.qx, w.px, w.tw[0]);
-    else
-      k_xfwd<R, 0><<<xblocks, kXThreads, xsm, st>>>(in, phase, damage, mt, w.spec, g, w.qx, w.px, w.tw[0]);
-    e = cudaGetLastError();
-  }
-  }
-  if (e != cudaSuccess) return e;
-  ++nl;
   if (g.ndim == 3) {
     const dim3 yg((g.nxh + w.ty - 1) / w.ty, g.nz, g.ncomp);
     const size_t ysm = (size_t)w.ty * g.ny * sizeof(C);
@@ -250,6 +221,48 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
     if (e != cudaSuccess) return e;
     ++nl;
   }
+  *nlp += nl;
+  return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>& mt, const R* in,
+                           const uint8_t* phase, const R* damage, XIn mode, R* out,
+                           const R* dot_with, double* dot_out, cudaStream_t st, long long* nlaunch) {
+  using C = Cx<R>;
+  constexpr bool F32 = std::is_same<R, float>::value;
+  long long nl = 0;
+  cudaError_t e;
+  const int xblocks = (int)((g.nrows + w.qx - 1) / w.qx);
+  const size_t xsm = (size_t)((g.ncomp * w.qx) / 2) * g.nx * sizeof(C);
+  // dot(in, G:B:in) for a compatible input (in = G:in, as every CG direction
+  // is) equals dot(in, B:in): the compiled x-forward pass forms it from the
+  // tangent it already computes, so the x-inverse need not read `in` again
+  bool fwd_dot = false;
+  int fwd_blocks = 0;
+  // x forward (tangent fused)
+  e = cudaErrorNotSupported;
+  {
+  PassScope ps(w.timer, st, PASS_XFWD);
+  if constexpr (F32) {
+    if (fast_size(g.nx)) {
+      const bool want = mode == XIn::Tangent && dot_with != nullptr && dot_with == in;
+      e = fast_xfwd(g, in, phase, damage, mt, w.spec, w.tw[0], mode == XIn::Tangent, want ? w.partials : nullptr,
+                    &fwd_blocks, st);
+      fwd_dot = want && e == cudaSuccess;
+    }
+  }
+  if (e == cudaErrorNotSupported) {
+    if (mode == XIn::Tangent)
+      k_xfwd<R, 1><<<xblocks, kXThreads, xsm, st>>>(in, phase, damage, mt, w.spec, g, w.qx, w.px, w.tw[0]);
+    else
+      k_xfwd<R, 0><<<xblocks, kXThreads, xsm, st>>>(in, phase, damage, mt, w.spec, g, w.qx, w.px, w.tw[0]);
+    e = cudaGetLastError();
+  }
+  }
+  if (e != cudaSuccess) return e;
+  ++nl;
+  if ((e = spectral_middle<R>(g, w, st, &nl)) != cudaSuccess) return e;
   const R scale = (R)(1.0 / (double)g.nvox);
   const bool dot = dot_with != nullptr && !fwd_dot;
   const bool self = dot && (dot_with == out);
@@ -278,6 +291,34 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
     e = reduce_partials(w.partials, fwd_dot ? fwd_blocks : nblocks, 1, dot_out, st, &nl);
     if (e != cudaSuccess) return e;
   }
+  if (nlaunch) *nlaunch += nl;
+  return cudaSuccess;
+}
+
+cudaError_t spectral_hv_cg(const GridDesc& g, SpecWork<float>& w, const MatTable<float>& mt, const float* d,
+                           const uint8_t* phase, const float* damage, float* z, float* r, double* dHd,
+                           cudaError_t (*between)(void*), void* between_arg, const int* status, const double* alpha,
+                           const double* tau, double* sums, cudaStream_t st, long long* nlaunch) {
+  if (!fast_size(g.nx)) return cudaErrorNotSupported;
+  long long nl = 0;
+  cudaError_t e;
+  int fb = 0, ib = 0;
+  {
+    PassScope ps(w.timer, st, PASS_XFWD);
+    e = fast_xfwd(g, d, phase, damage, mt, w.spec, w.tw[0], true, w.partials, &fb, st);
+  }
+  if (e != cudaSuccess) return e;
+  ++nl;
+  if ((e = reduce_partials(w.partials, fb, 1, dHd, st, &nl)) != cudaSuccess) return e;
+  if ((e = spectral_middle<float>(g, w, st, &nl)) != cudaSuccess) return e;
+  if ((e = between(between_arg)) != cudaSuccess) return e;
+  {
+    PassScope ps(w.timer, st, PASS_XINV);
+    e = fast_xinv_cg(g, w.spec, z, r, d, status, alpha, tau, w.partials, w.tw[0], &ib, st);
+  }
+  if (e != cudaSuccess) return e;
+  ++nl;
+  if ((e = reduce_partials(w.partials, ib, 3, sums, st, &nl)) != cudaSuccess) return e;
   if (nlaunch) *nlaunch += nl;
   return cudaSuccess;
 }

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <new>
 #include <string>
 #include <utility>
@@ -164,6 +165,18 @@ rve_status create_impl(rve_ctx* c, const uint8_t* phase_ids, const rve_phase* ph
   return RVE_OK;
 }
 
+// The CG step-length kernel, launched between the forward and the inverse
+// passes of the fused product.
+struct AlphaArg {
+  DevScalars* S;
+  cudaStream_t st;
+  long long* nl;
+};
+static cudaError_t launch_alpha(void* p) {
+  AlphaArg* a = static_cast<AlphaArg*>(p);
+  return cg_alpha(a->S, a->st, a->nl);
+}
+
 // Steihaug CG on H p = -g inside radius S.R (Algorithm 1).  Result in z,
 // exit status in S.status.
 template <typename R>
@@ -179,15 +192,27 @@ rve_status steihaug(rve_ctx* c, rve_step_report* rep) {
   if (s != RVE_OK) return s;
   if (c->Sh->status != CG_RUN) return RVE_OK;
   for (;;) {
-    CK(spectral_apply<R>(g, m->sw, m->mt, m->d, m->phase, m->D, XIn::Tangent, m->Hd, m->d, &m->S->dHd, c->st, nl),
-       "hessp");
-    ++c->hv;
-    if (rep) ++rep->hv_products;
-    CK(cg_alpha(m->S, c->st, nl), "cg alpha");
-    {
+    // product, step length and iterate / residual update; on the compiled
+    // FP32 x passes as one fused sequence that never stores H d
+    bool fused = false;
+    if constexpr (std::is_same<R, float>::value) {
+      AlphaArg aa{m->S, c->st, nl};
+      const cudaError_t e = spectral_hv_cg(g, m->sw, m->mt, m->d, m->phase, m->D, m->z, m->r, &m->S->dHd,
+                                           launch_alpha, &aa, &m->S->status, &m->S->alpha, &m->S->tau,
+                                           &m->S->rr_new, c->st, nl);
+      if (e == cudaSuccess) fused = true;
+      else if (e != cudaErrorNotSupported) CK(e, "hessp (fused CG)");
+    }
+    if (!fused) {
+      CK(spectral_apply<R>(g, m->sw, m->mt, m->d, m->phase, m->D, XIn::Tangent, m->Hd, m->d, &m->S->dHd, c->st,
+                           nl),
+         "hessp");
+      CK(cg_alpha(m->S, c->st, nl), "cg alpha");
       PassScope ps(&c->timer, c->st, PASS_CGVEC);
       CK(cg_update<R>(g, m->z, m->r, m->d, m->Hd, m->S, m->sw.partials, c->st, nl), "cg update");
     }
+    ++c->hv;
+    if (rep) ++rep->hv_products;
     CK(cg_beta(m->S, c->st, nl), "cg beta");
     s = read_scalars<R>(c);
     if (s != RVE_OK) return s;

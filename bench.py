@@ -261,9 +261,11 @@ def _pass_bytes(n, pass_name):
         "y_fwd": 2 * spec,
         "z_proj": 2 * spec,
         "y_inv": 2 * spec,
-        "x_inv": spec + field,  # the CG curvature dot is formed in the x-forward pass
+        # CG products: the x-inverse applies z += alpha d, r += alpha Hd (reads z, r, d;
+        # writes z, r) instead of storing Hd
+        "x_inv": spec + 5 * field,
         "trial": nvox * (24 + 24 + 4 + 24 + 4 + 1 + 24 + 4 + 4),
-        "cg_vec": nvox * 120,
+        "cg_vec": nvox * 96,  # direction update: reads z, r, d, writes d
     }.get(pass_name)
 
 

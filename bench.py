@@ -257,9 +257,7 @@ def _pass_bytes(n, pass_name):
     spec = 6 * n * n * (n // 2 + 1) * 8  # half spectrum, 6 complex components
     field = 6 * nvox * 4
     return {
-        # CG products after the first: forms d = -r + beta d (reads r, z, old d;
-        # writes d), applies the tangent (phase, damage) and writes the half spectrum
-        "xfwd_tangent": 4 * field + nvox * (1 + 4) + spec,
+        "xfwd_tangent": field + nvox * (1 + 4) + spec,
         "y_fwd": 2 * spec,
         "z_proj": 2 * spec,
         "y_inv": 2 * spec,
@@ -267,7 +265,7 @@ def _pass_bytes(n, pass_name):
         # writes z, r) instead of storing Hd
         "x_inv": spec + 5 * field,
         "trial": nvox * (24 + 24 + 4 + 24 + 4 + 1 + 24 + 4 + 4),
-        "cg_vec": nvox * 96,  # direction update (only where the fused passes do not apply)
+        "cg_vec": nvox * 96,  # direction update: reads z, r, d, writes d
     }.get(pass_name)
 
 

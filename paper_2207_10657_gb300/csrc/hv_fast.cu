@@ -31,18 +31,11 @@ template <int N> constexpr int zminblocks() { return N >= 512 ? 1 : 3; }
 template <int N> constexpr int p2tx() { return (kFBudget / (3 * N)) < 16 ? (kFBudget / (3 * N)) : 16; }
 
 // ------------------------------------------------------------ x forward
-// DIR (with MODE 1): the input is the CG direction after the update of
-// Algorithm 1, d = -r + beta d, formed here from r, the old d (read from
-// `dout`, which `in` aliases) and *beta, written back to `dout` and
-// transformed; the sums
-// d.d, z.d, r.d go to partials3[3 b + s].
-template <int N, int NC, int MODE, bool DIR = false>
+template <int N, int NC, int MODE>
 __global__ void __launch_bounds__(kFT)
     kf_xfwd(const float* __restrict__ in, const uint8_t* __restrict__ phase, const float* __restrict__ dmg,
             const MatTable<float> mt, float2* __restrict__ spec, const long long nrows, const long long nvox,
-            const float2* __restrict__ tw, double* __restrict__ partials, const float* __restrict__ rdir = nullptr,
-            const float* __restrict__ zdir = nullptr, const double* __restrict__ beta = nullptr,
-            float* dout = nullptr, double* __restrict__ partials3 = nullptr) {
+            const float2* __restrict__ tw, double* __restrict__ partials) {
   constexpr int Q = xq<N, NC>();
   constexpr int NL = NC * Q / 2;
   constexpr int ND = NC == 6 ? 3 : 2;
@@ -54,9 +47,7 @@ __global__ void __launch_bounds__(kFT)
   // so the line-interleaved shared-memory writes are (nearly) conflict free
   constexpr int ITEMS = Q * N;
   constexpr int STEPS = (ITEMS + kFT - 1) / kFT;
-  constexpr int BATCH = DIR ? (STEPS < 2 ? STEPS : 2) : (STEPS < 4 ? STEPS : 4);
-  float a_dd = 0.f, a_zd = 0.f, a_rd = 0.f;
-  const float bt = DIR ? (float)*beta : 0.f;
+  constexpr int BATCH = STEPS < 4 ? STEPS : 4;
   for (int s0 = 0; s0 < STEPS; s0 += BATCH) {
     float v[BATCH][NC];
 #pragma unroll
@@ -66,23 +57,8 @@ __global__ void __launch_bounds__(kFT)
       const long long row = row0 + q;
       const bool ok = (s0 + b < STEPS) && idx < ITEMS && row < nrows;
       const long long vox = row * N + x;
-      if constexpr (DIR) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const long long o = c * nvox + vox;
-          // the old direction is read through dout (in aliases it in this mode)
-          const float dold = ok ? dout[o] : 0.f, rv = ok ? __ldg(rdir + o) : 0.f, zv = ok ? __ldg(zdir + o) : 0.f;
-          const float dn = -rv + bt * dold;
-          if (ok) dout[o] = dn;
-          a_dd += dn * dn;
-          a_zd += zv * dn;
-          a_rd += rv * dn;
-          v[b][c] = dn;
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) v[b][c] = ok ? __ldg(in + c * nvox + vox) : 0.f;
-      }
+      for (int c = 0; c < NC; ++c) v[b][c] = ok ? __ldg(in + c * nvox + vox) : 0.f;
       if (MODE == 1 && ok) {
         const float keep = 1.f - __ldg(dmg + vox);
         const int ph = __ldg(phase + vox);
@@ -134,13 +110,6 @@ __global__ void __launch_bounds__(kFT)
     double val[1] = {(double)acc};
     block_sum<1>(val, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = val[0];
-  }
-  if constexpr (DIR) {
-    __shared__ double red3[3 * 32];
-    double v3[3] = {(double)a_dd, (double)a_zd, (double)a_rd};
-    block_sum<3>(v3, red3);
-    if (threadIdx.x == 0)
-      for (int k = 0; k < 3; ++k) partials3[3 * (long long)blockIdx.x + k] = v3[k];
   }
 }
 
@@ -441,26 +410,6 @@ static cudaError_t xfwd_n(const GridDesc& g, const float* in, const uint8_t* pha
 }
 
 template <int N>
-static cudaError_t xfwd_dir_n(const GridDesc& g, float* d, const float* r, const float* z, const double* beta,
-                              const uint8_t* phase, const float* dmg, const MatTable<float>& mt, float2* spec,
-                              const float2* tw, double* partials, double* partials3, int* nblocks, cudaStream_t st) {
-  if (g.ncomp == 6) {
-    constexpr int Q = xq<N, 6>();
-    const int blocks = (int)((g.nrows + Q - 1) / Q);
-    *nblocks = blocks;
-    kf_xfwd<N, 6, 1, true><<<blocks, kFT, 0, st>>>(d, phase, dmg, mt, spec, g.nrows, g.nvox, tw, partials, r, z,
-                                                   beta, d, partials3);
-  } else {
-    constexpr int Q = xq<N, 3>();
-    const int blocks = (int)((g.nrows + Q - 1) / Q);
-    *nblocks = blocks;
-    kf_xfwd<N, 3, 1, true><<<blocks, kFT, 0, st>>>(d, phase, dmg, mt, spec, g.nrows, g.nvox, tw, partials, r, z,
-                                                   beta, d, partials3);
-  }
-  return cudaGetLastError();
-}
-
-template <int N>
 static cudaError_t xinv_n(const GridDesc& g, const float2* spec, float* out, const float* dotw, double* partials,
                           const float2* tw, bool dot, bool self, int* nblocks, cudaStream_t st) {
   const float scale = (float)(1.0 / (double)g.nvox);
@@ -551,16 +500,6 @@ static cudaError_t xinv_cg_n(const GridDesc& g, const float2* spec, float* z, fl
                                                        false, z, r, d, status, alpha, tau);
   }
   return cudaGetLastError();
-}
-
-cudaError_t fast_xfwd_dir(const GridDesc& g, float* d, const float* r, const float* z, const double* beta,
-                          const uint8_t* phase, const float* dmg, const MatTable<float>& mt, float2* spec,
-                          const float2* tw, double* partials, double* partials3, int* nblocks, cudaStream_t st) {
-#define RVE_CASE(n_) \
-  if (g.nx == n_) return xfwd_dir_n<n_>(g, d, r, z, beta, phase, dmg, mt, spec, tw, partials, partials3, nblocks, st);
-  RVE_FAST_SIZES(RVE_CASE)
-#undef RVE_CASE
-  return cudaErrorNotSupported;
 }
 
 cudaError_t fast_xinv_cg(const GridDesc& g, const float2* spec, float* z, float* r, const float* d, const int* status,

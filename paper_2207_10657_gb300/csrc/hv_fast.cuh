@@ -15,12 +15,6 @@ cudaError_t fast_xfwd(const GridDesc& g, const float* in, const uint8_t* phase, 
                       int* nblocks, cudaStream_t st);
 cudaError_t fast_xinv(const GridDesc& g, const float2* spec, float* out, const float* dotw, double* partials,
                       const float2* tw, bool dot, bool self, int* nblocks, cudaStream_t st);
-// Tangent x-forward of the updated CG direction d = -r + (*beta) d (written
-// back to d): d:(tangent:d) per block in partials[b], d.d, z.d, r.d in
-// partials3[3 b + s].
-cudaError_t fast_xfwd_dir(const GridDesc& g, float* d, const float* r, const float* z, const double* beta,
-                          const uint8_t* phase, const float* dmg, const MatTable<float>& mt, float2* spec,
-                          const float2* tw, double* partials, double* partials3, int* nblocks, cudaStream_t st);
 // x-inverse that applies the Steihaug-CG iterate / residual update with the
 // product instead of storing it (status / alpha / tau: device scalars;
 // partials: three sums per block, block-major).

@@ -113,10 +113,9 @@ cudaError_t spectral_setup(const GridDesc& g, SpecWork<R>& w) {
     const int e2 = std::min(kYThreads * kYEpt, (int)(kSmemCap / sizeof(C)));
     w.tz = std::max(1, std::min(pow2_floor(std::max(1, e2 / (3 * g.ny))), 64));
   }
-  // up to four partial sums per x block (the fused CG passes: one curvature
-  // sum and three direction sums), and the compile-time x passes may take a
-  // single row per block (Nx = 512)
-  w.max_partials = (int)std::max<long long>(4 * g.nrows + 16, 4096 * 8);
+  // up to three partial sums per x block (the fused CG x-inverse), and the
+  // compile-time x passes may take a single row per block (Nx = 512)
+  w.max_partials = (int)std::max<long long>(3 * g.nrows + 8, 4096 * 8);
   if ((e = cudaMalloc(&w.partials, (size_t)w.max_partials * sizeof(double))) != cudaSuccess) return e;
   // opt in to large dynamic shared memory
   cudaFuncSetAttribute(k_xfwd<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
@@ -296,27 +295,21 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
   return cudaSuccess;
 }
 
-cudaError_t spectral_hv_cg(const GridDesc& g, SpecWork<float>& w, const MatTable<float>& mt, float* d,
-                           const uint8_t* phase, const float* damage, float* z, float* r, bool dir,
-                           const double* beta, double* dsums, double* dHd, cudaError_t (*between)(void*),
-                           void* between_arg, const int* status, const double* alpha, const double* tau,
-                           double* sums, cudaStream_t st, long long* nlaunch) {
+cudaError_t spectral_hv_cg(const GridDesc& g, SpecWork<float>& w, const MatTable<float>& mt, const float* d,
+                           const uint8_t* phase, const float* damage, float* z, float* r, double* dHd,
+                           cudaError_t (*between)(void*), void* between_arg, const int* status, const double* alpha,
+                           const double* tau, double* sums, cudaStream_t st, long long* nlaunch) {
   if (!fast_size(g.nx)) return cudaErrorNotSupported;
   long long nl = 0;
   cudaError_t e;
   int fb = 0, ib = 0;
-  double* p3 = w.partials + g.nrows + 8;  // direction sums after the (at most nrows) curvature partials
   {
     PassScope ps(w.timer, st, PASS_XFWD);
-    if (dir)
-      e = fast_xfwd_dir(g, d, r, z, beta, phase, damage, mt, w.spec, w.tw[0], w.partials, p3, &fb, st);
-    else
-      e = fast_xfwd(g, d, phase, damage, mt, w.spec, w.tw[0], true, w.partials, &fb, st);
+    e = fast_xfwd(g, d, phase, damage, mt, w.spec, w.tw[0], true, w.partials, &fb, st);
   }
   if (e != cudaSuccess) return e;
   ++nl;
   if ((e = reduce_partials(w.partials, fb, 1, dHd, st, &nl)) != cudaSuccess) return e;
-  if (dir && (e = reduce_partials(p3, fb, 3, dsums, st, &nl)) != cudaSuccess) return e;
   if ((e = spectral_middle<float>(g, w, st, &nl)) != cudaSuccess) return e;
   if ((e = between(between_arg)) != cudaSuccess) return e;
   {

@@ -48,14 +48,10 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
 // an exit) from the device scalars *status / *alpha / *tau, with r'.r',
 // r'.r, z'.z into sums[0..2].  Hd is never stored.  Returns
 // cudaErrorNotSupported (nothing launched) when Nx has no compiled pass.
-// With `dir`, the pass first forms the next direction d = -r + (*beta) d
-// (the update that closes the previous CG iteration), in place, with d.d,
-// z.d, r.d into dsums[0..2].
-cudaError_t spectral_hv_cg(const GridDesc& g, SpecWork<float>& w, const MatTable<float>& mt, float* d,
-                           const uint8_t* phase, const float* damage, float* z, float* r, bool dir,
-                           const double* beta, double* dsums, double* dHd, cudaError_t (*between)(void*),
-                           void* between_arg, const int* status, const double* alpha, const double* tau,
-                           double* sums, cudaStream_t st, long long* nlaunch);
+cudaError_t spectral_hv_cg(const GridDesc& g, SpecWork<float>& w, const MatTable<float>& mt, const float* d,
+                           const uint8_t* phase, const float* damage, float* z, float* r, double* dHd,
+                           cudaError_t (*between)(void*), void* between_arg, const int* status, const double* alpha,
+                           const double* tau, double* sums, cudaStream_t st, long long* nlaunch);
 
 template <typename R>
 cudaError_t spectral_setup(const GridDesc& g, SpecWork<R>& w);

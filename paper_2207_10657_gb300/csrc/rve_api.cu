@@ -191,19 +191,15 @@ rve_status steihaug(rve_ctx* c, rve_step_report* rep) {
   rve_status s = read_scalars<R>(c);
   if (s != RVE_OK) return s;
   if (c->Sh->status != CG_RUN) return RVE_OK;
-  bool first = true;
-  bool fused = false;
   for (;;) {
     // product, step length and iterate / residual update; on the compiled
-    // FP32 x passes as one fused sequence that never stores H d and that
-    // (after the first iteration) also applies the direction update that
-    // closed the previous iteration
-    fused = false;
+    // FP32 x passes as one fused sequence that never stores H d
+    bool fused = false;
     if constexpr (std::is_same<R, float>::value) {
       AlphaArg aa{m->S, c->st, nl};
-      const cudaError_t e = spectral_hv_cg(g, m->sw, m->mt, m->d, m->phase, m->D, m->z, m->r, !first,
-                                           &m->S->beta, &m->S->dd, &m->S->dHd, launch_alpha, &aa,
-                                           &m->S->status, &m->S->alpha, &m->S->tau, &m->S->rr_new, c->st, nl);
+      const cudaError_t e = spectral_hv_cg(g, m->sw, m->mt, m->d, m->phase, m->D, m->z, m->r, &m->S->dHd,
+                                           launch_alpha, &aa, &m->S->status, &m->S->alpha, &m->S->tau,
+                                           &m->S->rr_new, c->st, nl);
       if (e == cudaSuccess) fused = true;
       else if (e != cudaErrorNotSupported) CK(e, "hessp (fused CG)");
     }
@@ -228,11 +224,10 @@ rve_status steihaug(rve_ctx* c, rve_step_report* rep) {
       if (rep) ++rep->hv_products;
       CK(cg_restart<R>(g, m->r, m->tmp, m->g, m->S, m->sw.partials, c->st, nl), "cg restart");
     }
-    if (!fused) {
+    {
       PassScope ps(&c->timer, c->st, PASS_CGVEC);
       CK(cg_dupdate<R>(g, m->z, m->r, m->d, m->S, m->sw.partials, c->st, nl), "cg direction");
     }
-    first = false;
   }
   if (rep) {
     rep->cg_iters += c->Sh->iters;

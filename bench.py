@@ -64,9 +64,12 @@ def _args():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n", type=int, default=N, help="grid size (default 256)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="rve256", choices=["rve256", "batch96", "warmstart"],
+    p.add_argument("--workload", default="rve256", choices=["rve256", "batch96", "warmstart", "hv"],
                    help="rve256: the 256^3 sphere cell (default); batch96: 96 cells of uneven sizes; "
-                        "warmstart: train the spectral neural operator, then learned vs plain load steps")
+                        "warmstart: train the spectral neural operator, then learned vs plain load steps; "
+                        "hv: Hessian-vector products alone (damage snapshot, compatible input), several sizes")
+    p.add_argument("--hv-sizes", default="128,256,384", help="hv: cube edge lengths")
+    p.add_argument("--hv-precisions", default="32,64", help="hv: 32 and / or 64")
     p.add_argument("--ws-train-seconds", type=float, default=120.0,
                    help="warmstart: time budget of the training-data generation (plain solves at 64^3)")
     p.add_argument("--ws-iters", type=int, default=4000, help="warmstart: Adam iterations")
@@ -547,6 +550,62 @@ WS_WORKLOAD = ("learned warm start: 4-layer spectral neural operator (width 32, 
                "each to rel. residual 1e-6")
 
 
+HV_WORKLOAD = ("Hessian-vector products alone on the sphere cells of the load-step workload (48 spheres at "
+               "128^3, 144 at 256^3 and 384^3, r ~ U[4, 10], seed 0), damage snapshot D ~ U[0, 0.9] on the matrix "
+               "(seed 1), input v = G:(N(0,1) field, seed 2); 20 untimed products, then 200 timed one by one with "
+               "CUDA events on the solver's stream")
+
+
+def run_hv(args):
+    import numpy as np
+    import torch
+    from paper_2207_10657_gb300 import RVESolver, build as _build
+    from synth import damage_snapshot, random_field, random_spheres
+    _build.build()
+    peak, peak_kind = _peaks()
+    for n in (int(x) for x in args.hv_sizes.split(",")):
+        dims = (n, n, n)
+        nvox = n ** 3
+        pm = random_spheres(dims, count=48 if n <= 128 else 144, rmin=4.0, rmax=10.0, seed=0)
+        D = damage_snapshot(pm, dmax=0.9, seed=1)
+        for prec in (int(x) for x in args.hv_precisions.split(",")):
+            dt = torch.float32 if prec == 32 else torch.float64
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                s = RVESolver(dims, pm, [MATRIX, STIFF], precision=prec, stream=st)
+                s.set_damage(torch.from_numpy(D).to(device="cuda", dtype=dt))
+                v = s.project(torch.from_numpy(random_field(6, dims, seed=2)).to(device="cuda", dtype=dt))
+                out = s.field()
+            for _ in range(20):
+                s.hessp(v, out)
+            st.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(200)]
+            for e0, e1 in ev:
+                e0.record(st)
+                s.hessp(v, out)
+                e1.record(st)
+            st.synchronize()
+            ms = np.array([e0.elapsed_time(e1) for e0, e1 in ev])
+            es = prec // 8  # bytes per real
+            spec = 6 * n * n * (n // 2 + 1) * 2 * es
+            field = 6 * nvox * es
+            # plain product: x-forward (v, phase, damage -> spectrum), three spectral passes, x-inverse
+            byts = (field + nvox * (1 + es) + spec) + 3 * 2 * spec + (spec + field)
+            med = float(np.median(ms))
+            print(json.dumps({
+                "metric": "voxel-Hv/s (Hessian-vector product alone)", "value": nvox / (med / 1e3), "unit": UNIT,
+                "grid": [n, n, n], "dtype": f"f{prec}", "ms_median": med, "ms_p10": float(np.percentile(ms, 10)),
+                "ms_p90": float(np.percentile(ms, 90)), "products": len(ms),
+                "roofline": {"bound": "hbm", "achieved": byts / (med / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                             "frac": byts / (med / 1e3) / 1e9 / peak, "algorithmic_bytes": byts,
+                             "peak_source": peak_kind},
+                "config": {"workload": HV_WORKLOAD}}), flush=True)
+            s.close()
+            del v, out
+            torch.cuda.empty_cache()
+    return 0
+
+
 def run_warmstart(args):
     import numpy as np
     import torch
@@ -658,6 +717,8 @@ def main():
         return run_batch(args)
     if args.workload == "warmstart":
         return run_warmstart(args)
+    if args.workload == "hv":
+        return run_hv(args)
     return run_gpu(args)
 
 

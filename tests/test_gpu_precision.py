@@ -1,0 +1,94 @@
+"""Precision study (needs a GB300): the same load paths solved on the GPU with
+FP32 fields (FP64 reductions, CG scalars and ratio test) and with FP64
+everywhere, each against the FP64 oracle; the errors per result are printed
+(pytest -s) and bounded.
+
+FP32 fields cannot reach the 1e-8 residual of the FP64 runs (the rounding
+floor of an FP32 product is about 1e-7 relative), so they stop at 1e-6, the
+tolerance the FP32 load paths use everywhere else."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import circular_inclusion, random_spheres
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+MATRIX = (1.0, 0.3, True, 1e-4, 1e-3)
+
+
+def _oracle_curve(pm, phases, incs, free, prm):
+    from oracle.solver import load_path
+    orv = oracle.RVE(pm, [oracle.Phase(*p) if p[2] else oracle.Phase(p[0], p[1]) for p in phases], free_mask=free)
+    return load_path(orv, incs, prm)
+
+
+def _gpu_curve(dims, pm, phases, incs, free, precision, **opts):
+    from paper_2207_10657_gb300 import RVESolver, build
+    build.build()
+    s = RVESolver(dims, pm, phases, precision=precision, **opts)
+    sig, conv = [], []
+    for dE in incs:
+        rep = s.solve_step(dE, free_mask=free, raise_on_error=False)
+        conv.append(rep["converged"])
+        sig.append(rep["mean_stress"][:len(dE)])
+    eps = s.get_state()["eps"].cpu().numpy().astype(np.float64)
+    s.close()
+    return np.array(sig), conv, eps
+
+
+def test_precision_study_2d_softening_curve():
+    """Config 1 (32x32 plane strain, centred inclusion, eps_xx to 2e-3 in 20
+    increments, other components free)."""
+    from oracle.solver import TRParams
+    dims = (32, 32)
+    pm = circular_inclusion(dims, 0.3)
+    phases = [MATRIX, (10.0, 0.3, False, 0.0, 0.0)]
+    free = [0, 1, 1]
+    incs = [np.array([1e-4, 0, 0])] * 20
+    R0 = 10 * np.sqrt(32 * 32) * 1e-4
+    caps = dict(R0=R0, Rmax=R0, max_nr=400, max_cg=500)
+    ref = _oracle_curve(pm, phases, incs, np.array(free, bool), TRParams(eta_eq=1e-8, eta_cg=1e-10, **caps))
+    sref = ref["mean_stress"][:, 0]
+    scale = np.max(np.abs(sref))
+    s64, c64, _ = _gpu_curve(dims, pm, phases, incs, free, 64, eta_eq=1e-8, eta_cg=1e-10, **caps)
+    s32, c32, _ = _gpu_curve(dims, pm, phases, incs, free, 32, eta_eq=1e-6, eta_cg=1e-2, **caps)
+    e64 = np.abs(s64[:, 0] - sref) / scale
+    e32 = np.abs(s32[:, 0] - sref) / scale
+    print("\nincrement  sigma_xx(oracle)  err FP64  err FP32 (relative to max |sigma_xx|)")
+    for n in range(len(incs)):
+        print(f"{n + 1:9d}  {sref[n]: .6e}  {e64[n]:.2e}  {e32[n]:.2e}")
+    assert all(c64) and all(c32)
+    assert e64.max() < 1e-4
+    # FP32 stops at a 1e-6 residual; along the softening branch the
+    # difference grows with the damage increments it feeds
+    assert e32.max() < 1e-2
+
+
+def test_precision_study_3d_onset_of_damage():
+    """16^3 spheres in a damaging matrix, uniaxial eps_zz, two increments
+    (elastic, then the onset of damage): stress and final strain field."""
+    from oracle.solver import TRParams
+    dims = (16, 16, 16)
+    pm = random_spheres(dims, count=6, rmin=2.0, rmax=3.5, seed=7)
+    phases = [MATRIX, (10.0, 0.2, False, 0.0, 0.0)]
+    free = [1, 1, 0, 1, 1, 1]
+    incs = [np.array([0, 0, 4e-5, 0, 0, 0])] * 2
+    R0 = 10 * np.sqrt(16 ** 3) * 4e-5
+    caps = dict(R0=R0, Rmax=R0, max_nr=300)
+    ref = _oracle_curve(pm, phases, incs, np.array(free, bool), TRParams(eta_eq=1e-8, eta_cg=1e-2, **caps))
+    sref = ref["mean_stress"]
+    s64, c64, eps64 = _gpu_curve(dims, pm, phases, incs, free, 64, eta_eq=1e-8, eta_cg=1e-2, **caps)
+    s32, c32, eps32 = _gpu_curve(dims, pm, phases, incs, free, 32, eta_eq=1e-6, eta_cg=1e-2, **caps)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    print("\nincrement  |sigma| rel err FP64  FP32")
+    for n in range(len(incs)):
+        print(f"{n + 1:9d}  {rel(s64[n], sref[n]):.2e}  {rel(s32[n], sref[n]):.2e}")
+    print(f"strain field rel L2 err after the last increment: FP64 {rel(eps64, ref['eps']):.2e}  "
+          f"FP32 {rel(eps32, ref['eps']):.2e}")
+    assert all(c64) and all(c32)
+    assert max(rel(s64[n], sref[n]) for n in range(2)) < 1e-6
+    assert max(rel(s32[n], sref[n]) for n in range(2)) < 1e-4
+    assert rel(eps64, ref["eps"]) < 1e-6 and rel(eps32, ref["eps"]) < 1e-4

@@ -261,25 +261,17 @@ __global__ void __launch_bounds__(kFT)
   const int kx0 = blockIdx.x * TX;
   const int tv = min(TX, nxh - kx0);
   const long long plane = ((long long)blockIdx.z * nz + blockIdx.y) * N;
-  constexpr int STEPS = (N * TX + kFT - 1) / kFT;
-  float2 tmp[STEPS];
-#pragma unroll
-  for (int i = 0; i < STEPS; ++i) {
-    const int idx = threadIdx.x + i * kFT;
-    const int y = idx / TX, t = idx - (idx / TX) * TX;
-    tmp[i] = (idx < N * TX && t < tv) ? spec[(plane + y) * nxh + kx0 + t] : make_float2(0.f, 0.f);
-  }
-#pragma unroll
-  for (int i = 0; i < STEPS; ++i) {
-    const int idx = threadIdx.x + i * kFT;
-    if (idx < N * TX) buf[idx] = tmp[i];
-  }
-  __syncthreads();
-  fft_ct<N, TX, kFT, INV>(buf, tw);
-  for (int idx = threadIdx.x; idx < N * TX; idx += kFT) {
-    const int y = idx / TX, t = idx - (idx / TX) * TX;
-    if (t < tv) spec[(plane + y) * nxh + kx0 + t] = buf[idx];
-  }
+  // the first stage reads the columns straight from global memory and the
+  // last one writes them back: no staging through shared memory
+  auto load = [&](int t, int y) -> float2 {
+    return t < tv ? spec[(plane + y) * nxh + kx0 + t] : make_float2(0.f, 0.f);
+  };
+  auto store = [&](int t, int y, float2 v) {
+    if (t < tv) spec[(plane + y) * nxh + kx0 + t] = v;
+  };
+  fft_stage0_from<N, TX, kFT, INV>(buf, load);
+  fft_ct_range<N, TX, kFT, INV, 1, fft_nstages(N) - 1>(buf, tw);
+  fft_stage_last_to<N, TX, kFT, INV>(buf, tw, store);
 }
 
 // ------------------------------------------------- z + projection (3D)
@@ -296,27 +288,43 @@ __global__ void __launch_bounds__(zthreads<N>(), zminblocks<N>())
   float2* buf = reinterpret_cast<float2*>(smem_raw);
   const int kx0 = blockIdx.x * TX, ky = blockIdx.y;
   const int tv = min(TX, nxh - kx0);
-  constexpr int STEPS = (N * NL + NT - 1) / NT;
-  constexpr int LB = STEPS < 8 ? STEPS : 8;
-  for (int s0 = 0; s0 < STEPS; s0 += LB) {
-    float2 tmp[LB];
+  // line l = c * TX + t: component c, column kx0 + t
+  auto load = [&](int l, int z) -> float2 {
+    const int c = l / TX, t = l - (l / TX) * TX;
+    return t < tv ? spec[(((long long)c * N + z) * ny + ky) * nxh + kx0 + t] : make_float2(0.f, 0.f);
+  };
+  auto store = [&](int l, int z, float2 v) {
+    const int c = l / TX, t = l - (l / TX) * TX;
+    if (t < tv) spec[(((long long)c * N + z) * ny + ky) * nxh + kx0 + t] = v;
+  };
+  // The first forward stage reads straight from global memory and the last
+  // inverse stage writes straight back, where a thread's butterflies fit in
+  // registers (at most 24 complex values); otherwise the tile is staged
+  // through shared memory.
+  constexpr int R0 = fft_radix(N, 0);
+  constexpr bool DIRECT = ((NL * (N / R0) + NT - 1) / NT) * R0 <= 24;
+  if constexpr (DIRECT) {
+    fft_stage0_from<N, NL, NT, false>(buf, load);
+    fft_ct_range<N, NL, NT, false, 1, fft_nstages(N)>(buf, tw);
+  } else {
+    constexpr int STEPS = (N * NL + NT - 1) / NT;
+    constexpr int LB = STEPS < 8 ? STEPS : 8;
+    for (int s0 = 0; s0 < STEPS; s0 += LB) {
+      float2 tmp[LB];
 #pragma unroll
-    for (int b = 0; b < LB; ++b) {
-      const int idx = threadIdx.x + (s0 + b) * NT;
-      const int z = idx / NL, rem = idx - (idx / NL) * NL;
-      const int c = rem / TX, t = rem - (rem / TX) * TX;
-      tmp[b] = (s0 + b < STEPS && idx < N * NL && t < tv)
-                   ? spec[(((long long)c * N + z) * ny + ky) * nxh + kx0 + t]
-                   : make_float2(0.f, 0.f);
-    }
+      for (int b = 0; b < LB; ++b) {
+        const int idx = threadIdx.x + (s0 + b) * NT;
+        tmp[b] = (s0 + b < STEPS && idx < N * NL) ? load(idx - (idx / NL) * NL, idx / NL) : make_float2(0.f, 0.f);
+      }
 #pragma unroll
-    for (int b = 0; b < LB; ++b) {
-      const int idx = threadIdx.x + (s0 + b) * NT;
-      if (s0 + b < STEPS && idx < N * NL) buf[idx] = tmp[b];
+      for (int b = 0; b < LB; ++b) {
+        const int idx = threadIdx.x + (s0 + b) * NT;
+        if (s0 + b < STEPS && idx < N * NL) buf[idx] = tmp[b];
+      }
     }
+    __syncthreads();
+    fft_ct<N, NL, NT, false>(buf, tw);
   }
-  __syncthreads();
-  fft_ct<N, NL, NT, false>(buf, tw);
   const float2 ay = gay[ky], dy = gdy[ky];
   for (int pt = threadIdx.x; pt < N * TX; pt += NT) {
     const int z = pt / TX, t = pt - (pt / TX) * TX;
@@ -332,11 +340,13 @@ __global__ void __launch_bounds__(zthreads<N>(), zminblocks<N>())
     for (int c = 0; c < 6; ++c) buf[z * NL + c * TX + t] = m[c];
   }
   __syncthreads();
-  fft_ct<N, NL, NT, true>(buf, tw);
-  for (int idx = threadIdx.x; idx < N * NL; idx += NT) {
-    const int z = idx / NL, rem = idx - (idx / NL) * NL;
-    const int c = rem / TX, t = rem - (rem / TX) * TX;
-    if (t < tv) spec[(((long long)c * N + z) * ny + ky) * nxh + kx0 + t] = buf[idx];
+  // inverse z transform
+  if constexpr (DIRECT) {
+    fft_ct_range<N, NL, NT, true, 0, fft_nstages(N) - 1>(buf, tw);
+    fft_stage_last_to<N, NL, NT, true>(buf, tw, store);
+  } else {
+    fft_ct<N, NL, NT, true>(buf, tw);
+    for (int idx = threadIdx.x; idx < N * NL; idx += NT) store(idx - (idx / NL) * NL, idx / NL, buf[idx]);
   }
 }
 

@@ -41,7 +41,8 @@ def _rel(a, b):
 # 96/192/384) and mixtures of both, degenerate 2-point axes and a 1024 axis
 GRIDS = [(32, 24), (30, 40), (2, 2), (1024, 8), (8, 12, 10), (16, 16, 16), (24, 20, 18), (2, 2, 2),
          (6, 4, 1024), (96, 64), (512, 32), (32, 32, 32), (64, 32, 96), (128, 192, 8), (384, 6, 4),
-         (8, 10, 512), (256, 8, 128), (512, 4, 8), (8, 128, 256), (4, 512, 64), (64, 64, 64)]
+         (8, 10, 512), (256, 8, 128), (512, 4, 8), (8, 128, 256), (4, 512, 64), (64, 64, 64), (4, 6, 384),
+         (6, 4, 192), (4, 384, 6), (6, 96, 96)]
 
 
 @pytest.mark.parametrize("precision", [32, 64])

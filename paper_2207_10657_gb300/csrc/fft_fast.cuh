@@ -36,16 +36,12 @@ constexpr int fft_radix(int n, int s) {
                                                                             : 5;
 }
 constexpr int fft_span(int n, int s) { return s == 0 ? 1 : fft_span(n, s - 1) * fft_radix(n, s - 1); }
-// The same radices in reverse order (an inverse transform run in the
-// reverse order starts with the forward's last radix).
-template <bool REV> constexpr int fft_rad(int n, int s) { return REV ? fft_radix(n, fft_nstages(n) - 1 - s) : fft_radix(n, s); }
-template <bool REV> constexpr int fft_spn(int n, int s) { return s == 0 ? 1 : fft_spn<REV>(n, s - 1) * fft_rad<REV>(n, s - 1); }
 
 // One stage (see stockham_stage in common.cuh for the index scheme).
-template <int N, int NL, int NT, bool INV, int S, typename C, bool REV = false>
+template <int N, int NL, int NT, bool INV, int S, typename C>
 __device__ __forceinline__ void fft_stage_ct(C* buf, const C* __restrict__ tw) {
-  constexpr int R = fft_rad<REV>(N, S);
-  constexpr int NS = fft_spn<REV>(N, S);
+  constexpr int R = fft_radix(N, S);
+  constexpr int NS = fft_span(N, S);
   constexpr int NBL = N / R;
   constexpr int TOTAL = NL * NBL;
   constexpr int PER = (TOTAL + NT - 1) / NT;
@@ -85,11 +81,11 @@ __device__ __forceinline__ void fft_stage_ct(C* buf, const C* __restrict__ tw) {
 }
 
 // Stages [S, SEND) in shared memory.
-template <int N, int NL, int NT, bool INV, int S, int SEND, bool REV = false, typename C>
+template <int N, int NL, int NT, bool INV, int S, int SEND, typename C>
 __device__ __forceinline__ void fft_ct_range(C* buf, const C* __restrict__ tw) {
   if constexpr (S < SEND) {
-    fft_stage_ct<N, NL, NT, INV, S, C, REV>(buf, tw);
-    fft_ct_range<N, NL, NT, INV, S + 1, SEND, REV>(buf, tw);
+    fft_stage_ct<N, NL, NT, INV, S>(buf, tw);
+    fft_ct_range<N, NL, NT, INV, S + 1, SEND>(buf, tw);
   }
 }
 
@@ -129,11 +125,11 @@ __device__ __forceinline__ void fft_stage0_from(C* buf, LoadF load) {
 // Last stage reading `buf` and handing its outputs to store(line, element,
 // value) (global memory) instead of writing them back.  The caller has
 // synchronised after the previous stage.
-template <int N, int NL, int NT, bool INV, bool REV = false, typename C, typename StoreF>
+template <int N, int NL, int NT, bool INV, typename C, typename StoreF>
 __device__ __forceinline__ void fft_stage_last_to(const C* buf, const C* __restrict__ tw, StoreF store) {
   constexpr int S = fft_nstages(N) - 1;
-  constexpr int R = fft_rad<REV>(N, S);
-  constexpr int NS = fft_spn<REV>(N, S);
+  constexpr int R = fft_radix(N, S);
+  constexpr int NS = fft_span(N, S);
   constexpr int NBL = N / R;
   constexpr int TOTAL = NL * NBL;
   constexpr int PER = (TOTAL + NT - 1) / NT;

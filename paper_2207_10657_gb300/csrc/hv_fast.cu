@@ -275,78 +275,6 @@ __global__ void __launch_bounds__(kFT)
 }
 
 // ------------------------------------------------- z + projection (3D)
-// The forward transform's last stage, the projection and the first stage of
-// the inverse transform run in the registers of one thread: with the
-// inverse radices in reverse order its first stage has the forward's last
-// radix R and reads exactly the R frequencies j + r N/R that the forward's
-// last butterfly j produces, so a thread that takes butterfly j of all six
-// component lines of one column holds every component of those frequencies.
-template <int N, int TX, int NL, int NT>
-__device__ __forceinline__ void zproj_middle(float2* buf, const float2* __restrict__ tw, int kx0, int ky, int tv,
-                                             const float2* __restrict__ gdx, const float2* __restrict__ gax,
-                                             const float2* __restrict__ gdz, const float2* __restrict__ gaz,
-                                             float2 dy, float2 ay, unsigned free_mask) {
-  constexpr int S = fft_nstages(N) - 1;
-  constexpr int R = fft_radix(N, S);
-  constexpr int NS = fft_span(N, S);  // = N / R
-  constexpr int NBL = N / R;
-  constexpr int TSTEP = N / (NS * R);
-  constexpr int ITEMS = TX * NBL;
-  constexpr int PER = (ITEMS + NT - 1) / NT;
-  float2 v[PER][6][R];
-#pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int it = threadIdx.x + i * NT;
-    if ((ITEMS % NT) == 0 || it < ITEMS) {
-      const int t = it % TX, j = it / TX;
-      const int k = j % NS;
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        const int l = c * TX + t;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          float2 x = buf[(j + r * NBL) * NL + l];
-          if (NS > 1 && r > 0) x = cmul(x, __ldg(&tw[r * k * TSTEP]));
-          v[i][c][r] = x;
-        }
-        Dft<R, false, float2>::run(v[i][c]);  // v[i][c][r] = X[j + r NS]
-      }
-      if (t < tv) {
-        const int kx = kx0 + t;
-        const float2 ax = gax[kx], dx = gdx[kx];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int kz = j + r * NS;
-          const float2 az = gaz[kz], dz = gdz[kz];
-          float2 m[6];
-#pragma unroll
-          for (int c = 0; c < 6; ++c) m[c] = v[i][c][r];
-          project3<float>(m, cmul(cmul(dx, ay), az), cmul(cmul(ax, dy), az), cmul(cmul(ax, ay), dz),
-                          kx == 0 && ky == 0 && kz == 0, free_mask);
-#pragma unroll
-          for (int c = 0; c < 6; ++c) v[i][c][r] = m[c];
-        }
-      }
-      // first inverse stage of the reversed schedule: span 1, no twiddles
-#pragma unroll
-      for (int c = 0; c < 6; ++c) Dft<R, true, float2>::run(v[i][c]);
-    }
-  }
-  __syncthreads();  // every thread has read its inputs
-#pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int it = threadIdx.x + i * NT;
-    if ((ITEMS % NT) == 0 || it < ITEMS) {
-      const int t = it % TX, j = it / TX;
-#pragma unroll
-      for (int c = 0; c < 6; ++c)
-#pragma unroll
-        for (int r = 0; r < R; ++r) buf[(j * R + r) * NL + c * TX + t] = v[i][c][r];
-    }
-  }
-  __syncthreads();
-}
-
 template <int N>
 __global__ void __launch_bounds__(zthreads<N>(), zminblocks<N>())
     kf_zproj(float2* __restrict__ spec, const int ny, const int nxh, const float2* __restrict__ tw,
@@ -369,22 +297,15 @@ __global__ void __launch_bounds__(zthreads<N>(), zminblocks<N>())
     const int c = l / TX, t = l - (l / TX) * TX;
     if (t < tv) spec[(((long long)c * N + z) * ny + ky) * nxh + kx0 + t] = v;
   };
-  // Direct path, where a thread's butterflies fit in registers: the first
-  // forward stage reads straight from global memory, the forward's last
-  // stage, the projection and the inverse's first stage (radices in reverse
-  // order) run in registers (zproj_middle), and the last inverse stage writes
-  // straight back.  Otherwise the tile is staged through shared memory.
+  // The first forward stage reads straight from global memory and the last
+  // inverse stage writes straight back, where a thread's butterflies fit in
+  // registers (at most 24 complex values); otherwise the tile is staged
+  // through shared memory.
   constexpr int R0 = fft_radix(N, 0);
-  constexpr int RL = fft_radix(N, fft_nstages(N) - 1);
-  constexpr bool DIRECT = ((NL * (N / R0) + NT - 1) / NT) * R0 <= 24 && fft_nstages(N) >= 2 &&
-                          ((TX * (N / RL) + NT - 1) / NT) * 6 * RL <= 24;
+  constexpr bool DIRECT = ((NL * (N / R0) + NT - 1) / NT) * R0 <= 24;
   if constexpr (DIRECT) {
     fft_stage0_from<N, NL, NT, false>(buf, load);
-    fft_ct_range<N, NL, NT, false, 1, fft_nstages(N) - 1>(buf, tw);
-    zproj_middle<N, TX, NL, NT>(buf, tw, kx0, ky, tv, gdx, gax, gdz, gaz, gdy[ky], gay[ky], free_mask);
-    fft_ct_range<N, NL, NT, true, 1, fft_nstages(N) - 1, true>(buf, tw);
-    fft_stage_last_to<N, NL, NT, true, true>(buf, tw, store);
-    return;
+    fft_ct_range<N, NL, NT, false, 1, fft_nstages(N)>(buf, tw);
   } else {
     constexpr int STEPS = (N * NL + NT - 1) / NT;
     constexpr int LB = STEPS < 8 ? STEPS : 8;
@@ -419,9 +340,14 @@ __global__ void __launch_bounds__(zthreads<N>(), zminblocks<N>())
     for (int c = 0; c < 6; ++c) buf[z * NL + c * TX + t] = m[c];
   }
   __syncthreads();
-  // inverse z transform (staged path)
-  fft_ct<N, NL, NT, true>(buf, tw);
-  for (int idx = threadIdx.x; idx < N * NL; idx += NT) store(idx - (idx / NL) * NL, idx / NL, buf[idx]);
+  // inverse z transform
+  if constexpr (DIRECT) {
+    fft_ct_range<N, NL, NT, true, 0, fft_nstages(N) - 1>(buf, tw);
+    fft_stage_last_to<N, NL, NT, true>(buf, tw, store);
+  } else {
+    fft_ct<N, NL, NT, true>(buf, tw);
+    for (int idx = threadIdx.x; idx < N * NL; idx += NT) store(idx - (idx / NL) * NL, idx / NL, buf[idx]);
+  }
 }
 
 // ------------------------------------------------- y + projection (2D)

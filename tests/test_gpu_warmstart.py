@@ -4,7 +4,7 @@ the A/B against the plain method on a held-out, larger cell (needs a GB300).
 
 What the trained network gains: a starting increment closer to the
 converged one than the uniform predictor's; what it may not change: the
-converged result (the plain solver still judges convergence)."""
+converged result (the plain solver still decides convergence)."""
 import numpy as np
 import pytest
 

@@ -10,6 +10,14 @@ compatible v is G : (B : v).
 
 Norms and dot products are unnormalised Euclidean sums over every voxel and
 Mandel entry (so the trust radius scales with sqrt(#points), Sec. 3.2).
+
+Eigenstrain (Algorithm 2, and Sec. 3.3 for the ASR product sites): the
+material is evaluated at eps_eval = eps + eps_eig, where eps_eig is a
+per-phase Mandel vector gathered onto the voxels of that phase.  The
+unknown stays eps: the gradient, the Hessian and the convergence measures
+are those of eps; only the constitutive evaluation sees the shifted strain.
+The sign is the paper's (added to the strain), so a stress-free expansion e
+of a phase is eps_eig = -e.
 """
 import numpy as np
 
@@ -19,8 +27,9 @@ from .tensors import ncomp_of
 
 
 class RVE:
-    def __init__(self, phase_map, phases, free_mask=None, naive_dft=False):
+    def __init__(self, phase_map, phases, free_mask=None, naive_dft=False, eigenstrain=None):
         self.phase_map = np.asarray(phase_map)
+        self.nphase = len(phases)
         self.shape = self.phase_map.shape
         self.ndim = self.phase_map.ndim
         self.ncomp = ncomp_of(self.ndim)
@@ -29,6 +38,23 @@ class RVE:
         self.free_mask = (np.zeros(self.ncomp, dtype=bool) if free_mask is None
                           else np.asarray(free_mask, dtype=bool))
         self.naive = naive_dft
+        self.eig = None
+        self.set_eigenstrain(eigenstrain)
+
+    def set_eigenstrain(self, table):
+        """Per-phase eigenstrain table of shape (nphase, ncomp) (None: none),
+        gathered to a field (ncomp, *grid) on the voxels of each phase."""
+        if table is None:
+            self.eig = None
+            return
+        t = np.asarray(table, dtype=np.float64)
+        if t.shape != (self.nphase, self.ncomp):
+            raise ValueError(f"eigenstrain table must have shape {(self.nphase, self.ncomp)}")
+        self.eig = np.stack([t[self.phase_map, c] for c in range(self.ncomp)])
+
+    def eval_strain(self, eps):
+        """eps_eval = eps + eps_eig (Algorithm 2)."""
+        return eps if self.eig is None else eps + self.eig
 
     # -- linear algebra on fields -------------------------------------------
     @staticmethod
@@ -44,8 +70,9 @@ class RVE:
 
     # -- material ----------------------------------------------------------
     def stress(self, eps, kappa_hist):
-        """(sigma, D, kappa) at strain ``eps`` and committed history."""
-        return evaluate(eps, self.params, kappa_hist)
+        """(sigma, D, kappa) at strain ``eps`` and committed history, the
+        material evaluated at eps + eps_eig."""
+        return evaluate(self.eval_strain(eps), self.params, kappa_hist)
 
     def tangent(self, D, v):
         return tangent_apply(v, D, self.params.lam, self.params.mu)
@@ -60,8 +87,10 @@ class RVE:
         return self.G(sigma)
 
     def energy_frozen(self, eps, D):
-        """W = sum_Q 1/2 (1 - D) eps : C : eps with D frozen (Eq. (11))."""
-        return 0.5 * float(np.sum((1.0 - D) * eps * elastic_stress(eps, self.params.lam, self.params.mu)))
+        """W = sum_Q 1/2 (1 - D) e : C : e with D frozen and e = eps + eps_eig
+        (Eq. (11))."""
+        e = self.eval_strain(eps)
+        return 0.5 * float(np.sum((1.0 - D) * e * elastic_stress(e, self.params.lam, self.params.mu)))
 
     def mean(self, field):
         """Volume average of a Mandel field, shape (ncomp,)."""

@@ -210,9 +210,14 @@ def trust_region_step(prob, eps, hist, R, prm, record_iterates=False):
 
 
 def load_path(prob, increments, prm, eps0=None, hist0=None, warm_start=None,
-              on_step=None):
+              on_step=None, eigenstrains=None):
     """Ramp the macroscopic strain through ``increments`` (Mandel vectors
     applied uniformly, Algorithm 2's load loop) and return per-step results.
+
+    ``eigenstrains`` (optional, one entry per increment) holds the per-phase
+    eigenstrain table in force during that load step (Algorithm 2 adds it to
+    the strain before every constitutive evaluation; None keeps the
+    previous one).
 
     ``warm_start(step, eps) -> field or None`` may add a compatible initial
     fluctuation increment.  Returns dict with mean stresses, mean strains,
@@ -224,6 +229,8 @@ def load_path(prob, increments, prm, eps0=None, hist0=None, warm_start=None,
     out = dict(mean_stress=[], mean_strain=[], reports=[], kappa=None, eps=None, sigma=None)
     for n, dE in enumerate(increments):
         eps = eps + np.asarray(dE, dtype=np.float64).reshape((ncomp,) + (1,) * prob.ndim)
+        if eigenstrains is not None and eigenstrains[n] is not None:
+            prob.set_eigenstrain(eigenstrains[n])
         if warm_start is not None:
             w = warm_start(n, eps)
             if w is not None:

@@ -14,6 +14,7 @@ from .micro import (
     random_spheres,
     random_circles,
     laminate,
+    gel_sites,
     damage_snapshot,
     random_field,
     five_smooth_sizes,
@@ -25,6 +26,7 @@ __all__ = [
     "random_spheres",
     "random_circles",
     "laminate",
+    "gel_sites",
     "damage_snapshot",
     "random_field",
     "five_smooth_sizes",

@@ -9,6 +9,8 @@ aggregates, Sec. 3.3) are not available; these stand in for them:
 * ``random_circles`` -- the 2D analogue, stopped at a target area fraction.
 * ``laminate`` -- a two-layer laminate normal to one axis, interfaces on voxel
   faces.
+* ``gel_sites`` -- single voxels drawn at random inside one phase and given
+  another phase id (the ASR product sites inside aggregates, Sec. 3.3).
 * ``damage_snapshot`` -- a damage field drawn U[0, dmax] on damaging voxels.
 * ``random_field`` -- an N(0, 1) field with ``ncomp`` components.
 """
@@ -117,6 +119,19 @@ def laminate(dims, axis=2, frac=0.5):
     view = [1] * ndim
     view[ndim - 1 - axis] = n
     return np.broadcast_to(idx.reshape(view), shape).astype(np.uint8).copy()
+
+
+def gel_sites(phase, count, host=1, site=2, seed=3):
+    """Copy of ``phase`` with ``count`` distinct voxels of phase ``host``,
+    drawn uniformly without replacement, set to phase ``site``."""
+    rng = np.random.default_rng(seed)
+    out = np.array(phase, dtype=np.uint8, copy=True)
+    cand = np.flatnonzero(out == host)
+    if count > cand.size:
+        raise ValueError("more sites than host voxels")
+    pick = rng.choice(cand, size=count, replace=False)
+    out.reshape(-1)[pick] = site
+    return out
 
 
 def damage_snapshot(phase, damaging_phases=(0,), dmax=0.9, seed=1, dtype=np.float32):

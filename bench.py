@@ -20,6 +20,12 @@ ranks), ms_per_step = the load-step time.  The first increment stays below
 the damage threshold; later increments localise a crack band and take
 10^4-10^5 products each, too long for a bench run of minutes.
 
+--workload asr times the same kind of step on the cell read as an ASR-like
+concrete model (Sec. 3.3): the spheres as damaging aggregates in a damaging
+cement paste, single gel voxels inside the aggregates expanding by 5e-4 per
+step through the per-phase eigenstrain of Algorithm 2, all mean components
+stress-free.
+
 Roofline: the dominant kernel's average launch time comes from CUDA events
 recorded by the library around every launch inside the timed region;
 algorithmic bytes per launch are the compulsory reads + writes of that pass.
@@ -54,6 +60,17 @@ FREE = [1, 1, 0, 1, 1, 1]
 WORKLOAD = ("256^3 random-sphere RVE (144 spheres, r~U[4,10], seed 0; spheres E=10 nu=0.2 elastic, matrix "
             "E=1 nu=0.3 damaging kappa0=1e-4 kappaf=1e-3), uniaxial eps_zz increments 5e-5 (40 to 2e-3), "
             "other components stress-free, trust-region Newton + Steihaug CG to rel. residual 1e-6")
+# ASR-like cell (Sec. 3.3): Table 2's aggregate / cement paste / ASR product constants (E in GPa,
+# kappa0 = f_t / E, zero stiffness at 10 kappa0), gel voxels expanding by the paper's medium step
+ASR_STEP = 5e-4
+ASR_PHASES = [(12.0, 0.3, True, 2.5e-4, 2.5e-3), (59.0, 0.3, True, 10.0 / 59000.0, 100.0 / 59000.0),
+              (11.0, 0.18, False, 0.0, 0.0)]
+ASR_WORKLOAD = ("256^3 ASR-like cell: the 144 spheres of the load-step workload as aggregates (E=59 nu=0.3, "
+                "damaging, kappa0=f_t/E=1.69e-4, kappaf=10 kappa0) in a cement paste (E=12 nu=0.3, kappa0=2.5e-4, "
+                "kappaf=10 kappa0), 288 single gel voxels drawn inside the aggregates (E=11 nu=0.18, elastic) "
+                "with a stress-free expansion of 5e-4 per normal component (eigenstrain -5e-4, Algorithm 2), "
+                "every mean component stress-free (free expansion); a step = that expansion increment from the "
+                "unloaded cell, trust-region Newton + Steihaug CG to rel. residual 1e-6")
 
 
 def _args():
@@ -64,8 +81,9 @@ def _args():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n", type=int, default=N, help="grid size (default 256)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="rve256", choices=["rve256", "batch96", "warmstart", "hv"],
-                   help="rve256: the 256^3 sphere cell (default); batch96: 96 cells of uneven sizes; "
+    p.add_argument("--workload", default="rve256", choices=["rve256", "asr", "batch96", "warmstart", "hv"],
+                   help="rve256: the 256^3 sphere cell (default); asr: the same cell as an ASR-like "
+                        "aggregate / paste / gel model loaded by gel eigenstrain; batch96: 96 cells of uneven sizes; "
                         "warmstart: train the spectral neural operator, then learned vs plain load steps; "
                         "hv: Hessian-vector products alone (damage snapshot, compatible input), several sizes")
     p.add_argument("--hv-sizes", default="128,256,384", help="hv: cube edge lengths")
@@ -290,21 +308,33 @@ def run_gpu(args):
     if dist:
         dist.barrier()
     from paper_2207_10657_gb300 import RVESolver, binding
-    from synth import random_spheres
+    from synth import gel_sites, random_spheres
 
     n = args.n
     dims = (n, n, n)
     nvox = n ** 3
-    pm = random_spheres(dims, count=144 if n >= 256 else 48, rmin=4.0, rmax=10.0, seed=0)
+    nsph = 144 if n >= 256 else 48
+    pm = random_spheres(dims, count=nsph, rmin=4.0, rmax=10.0, seed=0)
+    asr = args.workload == "asr"
     st = torch.cuda.Stream()
-    with torch.cuda.stream(st):
-        s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, stream=st, eta_eq=1e-6, eta_cg=1e-2, max_nr=400)
-    dE = [0.0, 0.0, INC, 0.0, 0.0, 0.0]
+    if asr:
+        pm = gel_sites(pm, 2 * nsph, host=1, site=2, seed=3)
+        R0 = 10.0 * (nvox ** 0.5) * ASR_STEP
+        with torch.cuda.stream(st):
+            s = RVESolver(dims, pm, ASR_PHASES, precision=32, stream=st, eta_eq=1e-6, eta_cg=1e-2, max_nr=400,
+                          R0=R0, Rmax=R0)
+        s.set_eigenstrain([[0.0] * 6, [0.0] * 6, [-ASR_STEP] * 3 + [0.0] * 3])
+        dE, free, workload = [0.0] * 6, [1] * 6, ASR_WORKLOAD
+    else:
+        with torch.cuda.stream(st):
+            s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, stream=st, eta_eq=1e-6, eta_cg=1e-2,
+                          max_nr=400)
+        dE, free, workload = [0.0, 0.0, INC, 0.0, 0.0, 0.0], FREE, WORKLOAD
     eps0 = s.field(0.0)  # reference state: the unloaded cell
 
     def step():
         s.set_state(eps0)
-        return s.solve_step(dE, free_mask=FREE, raise_on_error=False)
+        return s.solve_step(dE, free_mask=free, raise_on_error=False)
 
     for _ in range(args.warmup):
         step()
@@ -355,7 +385,7 @@ def run_gpu(args):
         with torch.cuda.stream(st):
             dev_in.copy_(host_in, non_blocking=True)
         s.set_state(dev_in)
-        s.solve_step(dE, free_mask=FREE, raise_on_error=False)
+        s.solve_step(dE, free_mask=free, raise_on_error=False)
         binding.rve_get_state(s.h, dev_out.data_ptr())
         with torch.cuda.stream(st):
             host_out.copy_(dev_out, non_blocking=True)
@@ -396,13 +426,14 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [n, n, n], "parallelism": f"replicas x{ws}",
+        "config": {"workload": workload, "grid": [n, n, n], "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (each 6-component FP32 field is 403 MB > 129 MB L2)",
                    "hv_per_step": hv / args.steps,
                    "nr_iters_per_step": [r["nr_iters"] for r in timed],
                    "cg_iters_per_step": [r["cg_iters"] for r in timed],
                    "converged": [r["converged"] for r in timed],
                    "mean_stress_zz": [r["mean_stress"][2] for r in timed],
+                   "mean_strain_volumetric": [sum(r["mean_strain"][:3]) for r in timed],
                    "hv_only_ms": hv_only_ms / nprod,
                    "hv_only_voxel_hv_per_s": nvox / (hv_only_ms / nprod / 1e3),
                    "pass_ms_per_launch": {k: (v[1] / v[0] if v[0] else None) for k, v in stats.items()}},

@@ -128,6 +128,21 @@ rve_status rve_set_damage(rve_t, const void* damage_dev);
  * for Mandel component c.  Sets Ghat(0) = P_free (mixed control, Sec. 3.3). */
 rve_status rve_set_free_mask(rve_t, const uint8_t free_mask_host[6]);
 
+/* Per-phase eigenstrain (Algorithm 2: the constitutive law is evaluated at
+ * eps_eval = eps + eps_eig; Sec. 3.3 imposes a growing eigenstrain on the
+ * pixels holding ASR product under free expansion).  eig_host: host array of
+ * nphase x ncomp doubles, phase-major, Mandel order of the fields; nphase
+ * must equal the context's phase count.  Copied (the caller keeps
+ * ownership).  Every later constitutive evaluation (load steps, the initial
+ * state of a step, rve_energy_grad, rve_set_state) adds row p to the strain
+ * of the voxels of phase p; the unknown eps, the gradient G:sigma, the
+ * Hessian (secant at the damage so evaluated), the mean strain of the step
+ * report and the |d eps|/|eps| measure stay those of eps.  The current state
+ * (stress, damage, kappa) is re-evaluated at once.  The sign is the paper's:
+ * a stress-free expansion e of a phase is eps_eig = -e.  NULL removes the
+ * eigenstrain.  RVE_ERR_ARG on a wrong nphase or a non-finite entry. */
+rve_status rve_set_eigenstrain(rve_t, const double* eig_host, int nphase);
+
 /* Hessian-vector product of Eq. (8) with the secant tangent frozen at the
  * state: out = G : ((1 - D) C : v).  v_dev, out_dev: ncomp x Nvox real; they
  * may alias.  The product is: tangent (Eq. (13)), forward real FFT,

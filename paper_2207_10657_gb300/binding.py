@@ -53,6 +53,7 @@ _SIGS = [
                                      ctypes.c_void_p]),
     ("rve_set_damage", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("rve_set_free_mask", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint8)]),
+    ("rve_set_eigenstrain", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     ("rve_hessp", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("rve_project", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("rve_energy_grad", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
@@ -174,6 +175,17 @@ def rve_set_damage(h, damage_ptr):
 def rve_set_free_mask(h, mask):
     m = (ctypes.c_uint8 * 6)(*[1 if x else 0 for x in (list(mask) + [0] * (6 - len(mask)))])
     check(lib().rve_set_free_mask(h, m), h)
+
+
+def rve_set_eigenstrain(h, table):
+    """table: nphase rows of ncomp Mandel values (host), or None to remove."""
+    if table is None:
+        check(lib().rve_set_eigenstrain(h, None, 0), h)
+        return
+    rows = [list(map(float, r)) for r in table]
+    flat = [x for r in rows for x in r]
+    arr = (ctypes.c_double * len(flat))(*flat)
+    check(lib().rve_set_eigenstrain(h, arr, len(rows)), h)
 
 
 def rve_hessp(h, v_ptr, out_ptr):

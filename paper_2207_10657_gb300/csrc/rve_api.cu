@@ -41,6 +41,7 @@ template <typename R>
 struct Impl {
   SpecWork<R> sw;
   MatTable<R> mt;
+  EigTable<R> eg{};
   uint8_t* phase = nullptr;
   R *eps = nullptr, *sig = nullptr, *sig_t = nullptr, *g = nullptr, *z = nullptr, *r = nullptr, *d = nullptr,
     *Hd = nullptr, *tmp = nullptr;
@@ -158,7 +159,7 @@ rve_status create_impl(rve_ctx* c, const uint8_t* phase_ids, const rve_phase* ph
   CK(cudaMemsetAsync(m->khist, 0, ns, c->st), "memset");
   CK(cudaMemsetAsync(m->kap, 0, ns, c->st), "memset");
   // state eps = 0: sigma = 0, D = 0
-  CK(trial_eval<R>(g, m->mt, m->phase, m->eps, nullptr, m->khist, nullptr, nullptr, m->sig, m->D, m->kap, m->S,
+  CK(trial_eval<R>(g, m->mt, m->eg, m->phase, m->eps, nullptr, m->khist, nullptr, nullptr, m->sig, m->D, m->kap, m->S,
                    m->sw.partials, c->st, &c->launches),
      "initial state");
   CK(cudaStreamSynchronize(c->st), "synchronize");
@@ -271,7 +272,7 @@ rve_status solve_step_impl(rve_ctx* c, const double dE[6], const void* init, rve
        "warm start projection");
     CK(axpy<R>((long long)g.ncomp * g.nvox, (R)1, m->tmp, m->eps, c->st, nl), "warm start add");
   }
-  CK(trial_eval<R>(g, m->mt, m->phase, m->eps, nullptr, m->khist, nullptr, nullptr, m->sig, m->D, m->kap, m->S,
+  CK(trial_eval<R>(g, m->mt, m->eg, m->phase, m->eps, nullptr, m->khist, nullptr, nullptr, m->sig, m->D, m->kap, m->S,
                    m->sw.partials, c->st, nl),
      "stress");
   rve_status s = gradient<R>(c);
@@ -284,8 +285,8 @@ rve_status solve_step_impl(rve_ctx* c, const double dE[6], const void* init, rve
     if ((s = steihaug<R>(c, rp)) != RVE_OK) return s;
     {
       PassScope ps(&c->timer, c->st, PASS_TRIAL);
-      CK(trial_eval<R>(g, m->mt, m->phase, m->eps, m->z, m->khist, m->sig, m->D, m->sig_t, m->D_t, m->kap_t, m->S,
-                       m->sw.partials, c->st, nl),
+      CK(trial_eval<R>(g, m->mt, m->eg, m->phase, m->eps, m->z, m->khist, m->sig, m->D, m->sig_t, m->D_t, m->kap_t,
+                       m->S, m->sw.partials, c->st, nl),
          "trial stress");
     }
     CK(tr_decide(m->S, c->st, nl), "ratio test");
@@ -336,8 +337,26 @@ rve_status set_state_impl(rve_ctx* c, const void* strain, const void* khist) {
        "history copy");
   else
     CK(cudaMemsetAsync(m->khist, 0, (size_t)g.nvox * sizeof(R), c->st), "history reset");
-  CK(trial_eval<R>(g, m->mt, m->phase, m->eps, nullptr, m->khist, nullptr, nullptr, m->sig, m->D, m->kap, m->S,
+  CK(trial_eval<R>(g, m->mt, m->eg, m->phase, m->eps, nullptr, m->khist, nullptr, nullptr, m->sig, m->D, m->kap, m->S,
                    m->sw.partials, c->st, &c->launches),
+     "state stress");
+  return RVE_OK;
+}
+
+template <typename R>
+rve_status set_eig_impl(rve_ctx* c, const double* eig) {
+  Impl<R>* m = impl_of<R>(c);
+  const GridDesc& g = c->g;
+  EigTable<R> eg{};
+  if (eig)
+    for (int i = 0; i < m->mt.nphase; ++i)
+      for (int k = 0; k < g.ncomp; ++k) {
+        eg.e[i][k] = (R)eig[i * g.ncomp + k];
+        if (eig[i * g.ncomp + k] != 0.0) eg.on = 1;
+      }
+  m->eg = eg;
+  CK(trial_eval<R>(g, m->mt, m->eg, m->phase, m->eps, nullptr, m->khist, nullptr, nullptr, m->sig, m->D, m->kap,
+                   m->S, m->sw.partials, c->st, &c->launches),
      "state stress");
   return RVE_OK;
 }
@@ -358,7 +377,7 @@ template <typename R>
 rve_status energy_grad_impl(rve_ctx* c, const void* p, double* dW, double* dm, void* grad) {
   Impl<R>* m = impl_of<R>(c);
   const GridDesc& g = c->g;
-  CK(trial_eval<R>(g, m->mt, m->phase, m->eps, (const R*)p, m->khist, m->sig, m->D, m->sig_t, m->D_t, m->kap_t,
+  CK(trial_eval<R>(g, m->mt, m->eg, m->phase, m->eps, (const R*)p, m->khist, m->sig, m->D, m->sig_t, m->D_t, m->kap_t,
                    m->S, m->sw.partials, c->st, &c->launches),
      "trial stress");
   k_energy_s<<<1, 1, 0, c->st>>>(m->S);
@@ -478,6 +497,17 @@ rve_status rve_set_damage(rve_t c, const void* damage) {
   const size_t es = c->precision == 32 ? sizeof(float) : sizeof(double);
   CK(cudaMemcpyAsync(D, damage, (size_t)c->g.nvox * es, cudaMemcpyDeviceToDevice, c->st), "damage copy");
   return RVE_OK;
+}
+
+rve_status rve_set_eigenstrain(rve_t c, const double* eig, int nphase) {
+  if (!c) return RVE_ERR_ARG;
+  const int np = c->precision == 32 ? impl_of<float>(c)->mt.nphase : impl_of<double>(c)->mt.nphase;
+  if (eig) {
+    if (nphase != np) return fail(c, RVE_ERR_ARG, "nphase differs from the context's phase count");
+    for (int i = 0; i < nphase * c->g.ncomp; ++i)
+      if (!std::isfinite(eig[i])) return fail(c, RVE_ERR_ARG, "non-finite eigenstrain entry");
+  }
+  return DISPATCH(c, set_eig_impl, eig);
 }
 
 rve_status rve_set_free_mask(rve_t c, const uint8_t fm[6]) {

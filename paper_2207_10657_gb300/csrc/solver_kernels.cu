@@ -186,12 +186,13 @@ __global__ void __launch_bounds__(kVThreads)
 }
 
 // ------------------------------------------------------- constitutive
-// sigma_t = (1 - D_t) C : (eps + p), kappa_t = max(kappa_n, kappa(eps + p))
-// on damaging phases.  Sums (group T): sig0:p, sig_t:p, p:(1-D0)C:p,
-// sig_t:sig_t, p:p, (eps+p):(eps+p).
+// With e = eps + p + eps_eig(phase): sigma_t = (1 - D_t) C : e,
+// kappa_t = max(kappa_n, kappa(e)) on damaging phases.  Sums (group T):
+// sig0:p, sig_t:p, p:(1-D0)C:p, sig_t:sig_t, p:p, (eps+p):(eps+p).
 template <typename R, int NC>
 __global__ void __launch_bounds__(kVThreads)
-    k_trial(const GridDesc g, const MatTable<R> mt, const uint8_t* __restrict__ phase, const R* __restrict__ eps,
+    k_trial(const GridDesc g, const MatTable<R> mt, const EigTable<R> eg, const uint8_t* __restrict__ phase,
+            const R* __restrict__ eps,
             const R* __restrict__ p, const R* __restrict__ khist, const R* __restrict__ sig0,
             const R* __restrict__ D0, R* __restrict__ sig_t, R* __restrict__ D_t, R* __restrict__ kap_t,
             double* __restrict__ part) {
@@ -216,13 +217,14 @@ __global__ void __launch_bounds__(kVThreads)
     V4<R> sg[6], Dq, kq;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      R ev[6], pq[6];
+      const int ph = phs[q];
+      R ev[6], pq[6], et[6];
 #pragma unroll
       for (int c = 0; c < nc; ++c) {
         pq[c] = elc<R>(pv[c], q);
-        ev[c] = elc<R>(e[c], q) + pq[c];
+        et[c] = elc<R>(e[c], q) + pq[c];
+        ev[c] = eg.on ? et[c] + eg.e[ph][c] : et[c];
       }
-      const int ph = phs[q];
       const R lam = mt.lam[ph], mu = mt.mu[ph];
       R D = 0, kap = 0;
       if (mt.damaging[ph]) {
@@ -246,7 +248,7 @@ __global__ void __launch_bounds__(kVThreads)
         acc[2].add(pq[c] * bp);
         acc[3].add(sv * sv);
         acc[4].add(pq[c] * pq[c]);
-        acc[5].add(ev[c] * ev[c]);
+        acc[5].add(et[c] * et[c]);
       }
       el<R>(Dq, q) = D;
       el<R>(kq, q) = kap;
@@ -360,13 +362,15 @@ cudaError_t cg_dupdate(const GridDesc& g, const R* z, const R* r, R* d, DevScala
 }
 
 template <typename R>
-cudaError_t trial_eval(const GridDesc& g, const MatTable<R>& mt, const uint8_t* phase, const R* eps, const R* p,
-                       const R* khist, const R* sig0, const R* D0, R* sig_t, R* D_t, R* kap_t,
-                       DevScalars* S, double* part, cudaStream_t st, long long* nl) {
+cudaError_t trial_eval(const GridDesc& g, const MatTable<R>& mt, const EigTable<R>& eg, const uint8_t* phase,
+                       const R* eps, const R* p, const R* khist, const R* sig0, const R* D0, R* sig_t, R* D_t,
+                       R* kap_t, DevScalars* S, double* part, cudaStream_t st, long long* nl) {
   if (g.ncomp == 6)
-    k_trial<R, 6><<<kVBlocks, kVThreads, 0, st>>>(g, mt, phase, eps, p, khist, sig0, D0, sig_t, D_t, kap_t, part);
+    k_trial<R, 6><<<kVBlocks, kVThreads, 0, st>>>(g, mt, eg, phase, eps, p, khist, sig0, D0, sig_t, D_t, kap_t,
+                                                  part);
   else
-    k_trial<R, 3><<<kVBlocks, kVThreads, 0, st>>>(g, mt, phase, eps, p, khist, sig0, D0, sig_t, D_t, kap_t, part);
+    k_trial<R, 3><<<kVBlocks, kVThreads, 0, st>>>(g, mt, eg, phase, eps, p, khist, sig0, D0, sig_t, D_t, kap_t,
+                                                  part);
   RVE_TRY(cudaGetLastError());
   *nl += 1;
   return reduce_partials(part, kVBlocks, 6, &S->sp, st, nl);
@@ -412,7 +416,8 @@ cudaError_t field_means(const GridDesc& g, const R* sig, const R* eps, DevScalar
                                      cudaStream_t, long long*);                                                 \
   template cudaError_t cg_dupdate<R>(const GridDesc&, const R*, const R*, R*, DevScalars*, double*,            \
                                      cudaStream_t, long long*);                                                 \
-  template cudaError_t trial_eval<R>(const GridDesc&, const MatTable<R>&, const uint8_t*, const R*, const R*,   \
+  template cudaError_t trial_eval<R>(const GridDesc&, const MatTable<R>&, const EigTable<R>&, const uint8_t*, \
+                                     const R*, const R*,                                                        \
                                      const R*, const R*, const R*, R*, R*, R*, DevScalars*,                     \
                                      double*, cudaStream_t, long long*);                                        \
   template cudaError_t axpy<R>(long long, R, const R*, R*, cudaStream_t, long long*);                          \

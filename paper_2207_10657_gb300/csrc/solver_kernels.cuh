@@ -41,6 +41,15 @@ struct DevScalars {
   double msig[6], meps[6];
 };
 
+// Per-phase eigenstrain (Algorithm 2: the constitutive law is evaluated at
+// eps + eps_eig; Sec. 3.3 imposes it on the ASR product sites).  Passed by
+// value to the constitutive kernel; `on` is 0 when every entry is zero.
+template <typename R>
+struct EigTable {
+  int on;
+  R e[kMaxPhases][6];
+};
+
 template <typename R>
 struct FieldPtrs {
   GridDesc g;
@@ -69,10 +78,13 @@ template <typename R>
 cudaError_t cg_dupdate(const GridDesc& g, const R* z, const R* r, R* d, DevScalars* S, double* part,
                        cudaStream_t st, long long* nl);
 
-// Trial constitutive evaluation at eps + p (p may be NULL): sigma_t, D_t,
-// kappa_t, and group T sums against the stored state (sig0, D0, may be NULL).
+// Trial constitutive evaluation at eps + p (p may be NULL), the material seeing
+// eps + p + eps_eig(phase): sigma_t, D_t, kappa_t, and group T sums against the
+// stored state (sig0, D0, may be NULL); the strain norm (eps+p):(eps+p) of the
+// group excludes the eigenstrain.
 template <typename R>
-cudaError_t trial_eval(const GridDesc& g, const MatTable<R>& mt, const uint8_t* phase, const R* eps, const R* p,
+cudaError_t trial_eval(const GridDesc& g, const MatTable<R>& mt, const EigTable<R>& eg, const uint8_t* phase,
+                       const R* eps, const R* p,
                        const R* khist, const R* sig0, const R* D0, R* sig_t, R* D_t, R* kap_t,
                        DevScalars* S, double* part, cudaStream_t st, long long* nl);
 // rho_bar, radius update and acceptance (1 thread).

@@ -108,6 +108,17 @@ class RVESolver:
     def set_free_mask(self, mask):
         B.rve_set_free_mask(self.h, mask)
 
+    def set_eigenstrain(self, table):
+        """Per-phase eigenstrain (nphase rows of ncomp Mandel values) added to
+        the strain before every constitutive evaluation (Algorithm 2); None
+        removes it.  A stress-free expansion e of a phase is a row of -e."""
+        if table is not None:
+            rows = [list(r) for r in table]
+            if len(rows) != len(self.phases) or any(len(r) != self.ncomp for r in rows):
+                raise ValueError(f"eigenstrain table must be {len(self.phases)} x {self.ncomp}")
+            table = rows
+        B.rve_set_eigenstrain(self.h, table)
+
     def energy_grad(self, p=None, want_grad=True):
         grad = self.field() if want_grad else None
         dW, dm = B.rve_energy_grad(self.h, self._chk(p) if p is not None else 0,

@@ -228,18 +228,21 @@ def test_uniform_eigenstrain_equals_shifted_load_128cube_fp32():
     dims = (128, 128, 128)
     pm = random_spheres(dims, count=48, rmin=4.0, rmax=10.0, seed=0)
     phases = [(1.0, 0.3, True, 1e-4, 1e-3), (10.0, 0.2, False, 0.0, 0.0)]
-    e = np.array([2e-5, -1e-5, 3e-5, 0.5e-5, 0.0, -0.5e-5])
-    E = np.array([1e-5, 0.5e-5, 2e-5, 0.0, 0.5e-5, 0.0])
+    # elastic magnitudes (kappa stays below kappa0 = 1e-4 at the sphere
+    # interfaces), so both paths converge in a few Newton iterations
+    e = np.array([6e-6, -3e-6, 9e-6, 1.5e-6, 0.0, -1.5e-6])
+    E = np.array([3e-6, 1.5e-6, 6e-6, 0.0, 1.5e-6, 0.0])
     R0 = 10 * np.sqrt(pm.size) * np.linalg.norm(E + e)
     opts = dict(eta_eq=1e-6, eta_cg=1e-2, R0=R0, Rmax=R0, max_nr=100)
     sa = _solver(dims, pm, phases, 32, **opts)
     sa.set_eigenstrain(np.repeat(e[None, :], 2, 0))
-    ra = sa.solve_step(E, free_mask=[0] * 6)
+    ra = sa.solve_step(E, free_mask=[0] * 6, raise_on_error=False)
     ea = sa.get_state()
     sb = _solver(dims, pm, phases, 32, **opts)
-    rb = sb.solve_step(E + e, free_mask=[0] * 6)
+    rb = sb.solve_step(E + e, free_mask=[0] * 6, raise_on_error=False)
     eb = sb.get_state()
-    assert ra["converged"] and rb["converged"]
+    assert ra["converged"] and rb["converged"], (ra, rb)
+    assert float(ea["kappa"].max()) < 1e-4
     shift = torch.tensor(e, dtype=torch.float32, device=ea["eps"].device).view(6, 1, 1, 1)
     num = torch.linalg.vector_norm((ea["eps"] + shift - eb["eps"]).double())
     assert float(num / torch.linalg.vector_norm(eb["eps"].double())) < 1e-4

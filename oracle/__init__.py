@@ -9,7 +9,9 @@ It restates the paper's method in the most direct form that can be checked by
 eye: full complex DFTs (numpy's FFT, or a naive O(N^2)-per-axis DFT on tiny
 grids), the projection written per frequency, the constitutive law per voxel,
 and the two algorithms (Steihaug CG, trust-region Newton with the first-order
-incremental energy) step by step in the paper's order.  Every function cites
+incremental energy) step by step in the paper's order; ``lbfgs`` holds the
+quasi-Newton alternative the paper mentions (L-BFGS with the first-order
+energy in its line search).  Every function cites
 the section / equation / algorithm it follows.
 
 Equation numbers follow the paper's sequential numbering: (1) strain split,
@@ -50,6 +52,7 @@ from .material import (
 )
 from .rve import RVE
 from .solver import steihaug_cg, TRParams, trust_region_step, load_path
+from .lbfgs import LBFGSParams, lbfgs_step, load_path_lbfgs, two_loop
 
 __all__ = [
     "mandel_to_tensor", "tensor_to_mandel", "ncomp_of", "normal_comps",
@@ -57,4 +60,5 @@ __all__ = [
     "Phase", "lame", "PhaseParams", "elastic_stress", "principal_strains",
     "kappa_of_strain", "damage_of_kappa", "evaluate", "tangent_apply",
     "RVE", "steihaug_cg", "TRParams", "trust_region_step", "load_path",
+    "LBFGSParams", "lbfgs_step", "load_path_lbfgs", "two_loop",
 ]

@@ -26,6 +26,11 @@ cement paste, single gel voxels inside the aggregates expanding by 5e-4 per
 step through the per-phase eigenstrain of Algorithm 2, all mean components
 stress-free.
 
+--workload lbfgs solves the default load step by L-BFGS (the quasi-Newton
+method the first-order incremental energy makes usable, with Eq. (18) in its
+line search) and by the trust-region solver, and prints the L-BFGS step time
+with the trust-region time beside it.
+
 Roofline: the dominant kernel's average launch time comes from CUDA events
 recorded by the library around every launch inside the timed region;
 algorithmic bytes per launch are the compulsory reads + writes of that pass.
@@ -81,11 +86,14 @@ def _args():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n", type=int, default=N, help="grid size (default 256)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="rve256", choices=["rve256", "asr", "batch96", "warmstart", "hv"],
+    p.add_argument("--workload", default="rve256",
+                   choices=["rve256", "asr", "lbfgs", "batch96", "warmstart", "hv"],
                    help="rve256: the 256^3 sphere cell (default); asr: the same cell as an ASR-like "
-                        "aggregate / paste / gel model loaded by gel eigenstrain; batch96: 96 cells of uneven sizes; "
+                        "aggregate / paste / gel model loaded by gel eigenstrain; lbfgs: the default load step "
+                        "solved by L-BFGS and by trust-region Newton-CG; batch96: 96 cells of uneven sizes; "
                         "warmstart: train the spectral neural operator, then learned vs plain load steps; "
                         "hv: Hessian-vector products alone (damage snapshot, compatible input), several sizes")
+    p.add_argument("--lbfgs-memory", type=int, default=5, help="lbfgs: (s, y) pairs kept")
     p.add_argument("--hv-sizes", default="128,256,384", help="hv: cube edge lengths")
     p.add_argument("--hv-precisions", default="32,64", help="hv: 32 and / or 64")
     p.add_argument("--ws-train-seconds", type=float, default=120.0,
@@ -576,6 +584,73 @@ def run_batch(args):
     return 0
 
 
+def run_lbfgs(args):
+    """The default load step (256^3 sphere cell, first increment from the
+    unloaded state) solved by L-BFGS with the first-order energy line search
+    and by trust-region Newton-CG, timed alike (CUDA events, K steps)."""
+    import torch
+    from paper_2207_10657_gb300 import RVESolver, build as _build
+    from synth import random_spheres
+    _build.build()
+    n = args.n
+    dims = (n, n, n)
+    pm = random_spheres(dims, count=144 if n >= 256 else 48, rmin=4.0, rmax=10.0, seed=0)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, stream=st, eta_eq=1e-6, eta_cg=1e-2, max_nr=400)
+    dE = [0.0, 0.0, INC, 0.0, 0.0, 0.0]
+    eps0 = s.field(0.0)
+
+    def lb_step():
+        s.set_state(eps0)
+        return s.solve_step_lbfgs(dE, free_mask=FREE, memory=args.lbfgs_memory, max_iter=5000,
+                                  raise_on_error=False)
+
+    def tr_step():
+        s.set_state(eps0)
+        return s.solve_step(dE, free_mask=FREE, raise_on_error=False)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = s.launch_count
+        ev0.record(st)
+        reps = [fn() for _ in range(args.steps)]
+        ev1.record(st)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / args.steps, reps, s.launch_count - l0
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    lb_ms, lb_reps, lb_launch = timed(lb_step)
+    clocks = sampler.stop()
+    tr_ms, tr_reps, _ = timed(tr_step)
+    s.close()
+    line = {
+        "metric": "load-step time at 256³: L-BFGS (first-order energy line search) vs trust-region Newton-CG",
+        "value": lb_ms, "unit": "ms/load step", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": lb_ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD + "; the same load step by L-BFGS (memory "
+                   f"{args.lbfgs_memory}) and by the trust-region solver",
+                   "l2": "inputs larger than L2 (each 6-component FP32 field is 403 MB > 129 MB L2)",
+                   "lbfgs_iters_per_step": [r["nr_iters"] for r in lb_reps],
+                   "lbfgs_trials_per_step": [r["cg_iters"] for r in lb_reps],
+                   "lbfgs_halvings_per_step": [r["rejected"] for r in lb_reps],
+                   "lbfgs_converged": [r["converged"] for r in lb_reps],
+                   "lbfgs_mean_stress_zz": [r["mean_stress"][2] for r in lb_reps],
+                   "trust_region_ms_per_step": tr_ms,
+                   "trust_region_hv_per_step": [r["hv_products"] for r in tr_reps],
+                   "trust_region_mean_stress_zz": [r["mean_stress"][2] for r in tr_reps],
+                   "speedup_over_trust_region": tr_ms / lb_ms},
+        "gpu_launches": lb_launch, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 WS_WORKLOAD = ("learned warm start: 4-layer spectral neural operator (width 32, modes kx<16, |ky|,|kz|<=8, BF16 "
                "operands, FP32 accumulation) trained on plain-solver load steps of seeded 64^3 sphere cells (48 "
                "spheres, r~U[2,5]) under uniaxial eps_zz increments of 1e-5 (other components stress-free), then "
@@ -753,6 +828,8 @@ def main():
         return run_warmstart(args)
     if args.workload == "hv":
         return run_hv(args)
+    if args.workload == "lbfgs":
+        return run_lbfgs(args)
     return run_gpu(args)
 
 

@@ -96,7 +96,7 @@ void rve_default_opts(rve_solver_opts* opts);
 /* Create a context.  Sec. 2 (cell, strain split), Appendix A (phases).
  *  dims, ndim     grid (see conventions); ndim 2 = plane strain.
  *  phase_ids_dev  Nvox uint8 phase ids (device); copied, may be freed after.
- *  phases_host    nphase entries (1..255), copied.
+ *  phases_host    nphase entries (1..16), copied.
  *  opts_host      may be NULL for defaults; copied.
  *  stream         cudaStream_t (as void*) all work is issued on; NULL =
  *                 the legacy default stream.
@@ -171,6 +171,31 @@ rve_status rve_energy_grad(rve_t, const void* p_dev, double* dW_bar_host, double
  * (state kept, history not committed) when max_nr is exhausted. */
 rve_status rve_solve_step(rve_t, const double dE_host[6], const uint8_t free_mask_host[6],
                           const void* init_incr_dev, rve_step_report* rep_host);
+
+/* One load step solved by L-BFGS instead of the trust-region Newton-CG
+ * iteration: the quasi-Newton method that the paper notes becomes usable
+ * once the first-order incremental energy (Eq. (18)) stands in for the
+ * objective (Sec. 2.2.1, after Eq. (20)); no algorithm is printed, so this is
+ * Nocedal & Wright's L-BFGS (Alg. 7.5, two-loop recursion Alg. 7.4) on the
+ * compatible strain fields with gradient G:sigma and a backtracking Armijo
+ * line search on dW_bar: halve s = alpha p (alpha from 1, at most 40 times)
+ * until 1/2 (sigma(eps) + sigma(eps + s)) : s <= 1e-4 sigma(eps) : s.  A pair
+ * (s, y = G:sigma_new - G:sigma) is kept when s.y > 1e-12 |s||y|; H0 =
+ * gamma I with gamma = s.y / y.y of the newest pair, 1 / max_phase(3 lambda
+ * + 2 mu) before the first.  A direction that is not a descent direction
+ * drops the pairs.  Converged when |G:sigma| / |sigma| <= opts.eta_eq.
+ *  dE_host, free_mask_host  as for rve_solve_step (mask may be NULL)
+ *  memory        pairs kept, 1..16; 2 * memory fields of ncomp x Nvox reals
+ *                are allocated at the first call with that memory and kept
+ *  max_iter      iteration cap (>= 1)
+ *  rep_host      may be NULL; nr_iters = iterations, cg_iters = line-search
+ *                trials, rejected = step halvings, restarts = skipped pairs,
+ *                boundary_hits = pair resets, hv_products = 0, R = last alpha
+ * The history is committed on convergence as in rve_solve_step.
+ * RVE_ERR_ARG on a bad memory / max_iter; RVE_ERR_NOT_CONVERGED (state kept,
+ * history not committed) when max_iter is reached or the line search fails. */
+rve_status rve_solve_step_lbfgs(rve_t, const double dE_host[6], const uint8_t free_mask_host[6],
+                                int memory, int max_iter, rve_step_report* rep_host);
 
 /* Per-pass device timing, for benchmarks (not part of the method).
  * Pass ids: 0 x-forward FFT with the fused tangent, 1 y-forward FFT,

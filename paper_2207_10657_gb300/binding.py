@@ -61,6 +61,9 @@ _SIGS = [
     ("rve_solve_step", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_uint8), ctypes.c_void_p,
                                       ctypes.POINTER(rve_step_report)]),
+    ("rve_solve_step_lbfgs", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(rve_step_report)]),
     ("rve_pass_timing", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("rve_pass_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
@@ -210,6 +213,18 @@ def rve_solve_step(h, dE, free_mask=None, init_ptr=0, raise_on_error=True):
         fm = (ctypes.c_uint8 * 6)(*[1 if x else 0 for x in (list(free_mask) + [0] * (6 - len(free_mask)))])
     rep = rve_step_report()
     st = lib().rve_solve_step(h, de, fm, ctypes.c_void_p(init_ptr or None), ctypes.byref(rep))
+    if raise_on_error:
+        check(st, h)
+    return st, rep
+
+
+def rve_solve_step_lbfgs(h, dE, free_mask=None, memory=5, max_iter=500, raise_on_error=True):
+    de = (ctypes.c_double * 6)(*(list(dE) + [0.0] * (6 - len(dE))))
+    fm = None
+    if free_mask is not None:
+        fm = (ctypes.c_uint8 * 6)(*[1 if x else 0 for x in (list(free_mask) + [0] * (6 - len(free_mask)))])
+    rep = rve_step_report()
+    st = lib().rve_solve_step_lbfgs(h, de, fm, int(memory), int(max_iter), ctypes.byref(rep))
     if raise_on_error:
         check(st, h)
     return st, rep

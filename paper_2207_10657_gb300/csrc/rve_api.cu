@@ -3,6 +3,7 @@
 // The control loop runs on the host; every arithmetic step (fields and
 // FP64 scalars) runs in the kernels of hv_passes.cu and solver_kernels.cu,
 // and the host only reads back the small scalar block to branch.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -14,6 +15,7 @@
 
 #include "../../include/rve.h"
 #include "hv_passes.cuh"
+#include "lbfgs.cuh"
 #include "solver_kernels.cuh"
 
 using namespace rve;
@@ -47,6 +49,12 @@ struct Impl {
     *Hd = nullptr, *tmp = nullptr;
   R *D = nullptr, *D_t = nullptr, *kap = nullptr, *kap_t = nullptr, *khist = nullptr;
   DevScalars* S = nullptr;
+  // L-BFGS pairs (allocated at the first L-BFGS step; lb_mem of each)
+  int lb_mem = 0;
+  R* lbS[kLbMaxMemory] = {};
+  R* lbY[kLbMaxMemory] = {};
+  LbScalars* L = nullptr;
+  LbScalars* Lh = nullptr;  // pinned host mirror
 };
 
 bool five_smooth_even(int n) {
@@ -106,6 +114,12 @@ void impl_free(Impl<R>* m) {
                   m->D, m->D_t, m->kap, m->kap_t, m->khist, m->S};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (int i = 0; i < kLbMaxMemory; ++i) {
+    if (m->lbS[i]) cudaFree(m->lbS[i]);
+    if (m->lbY[i]) cudaFree(m->lbY[i]);
+  }
+  if (m->L) cudaFree(m->L);
+  if (m->Lh) cudaFreeHost(m->Lh);
   delete m;
 }
 
@@ -321,6 +335,181 @@ rve_status solve_step_impl(rve_ctx* c, const double dE[6], const void* init, rve
   rp->converged = converged ? 1 : 0;
   if (!converged) return fail(c, RVE_ERR_NOT_CONVERGED, "load step did not converge within max_nr");
   // commit history: kappa_n <- max(kappa_n, kappa(eps)) (kap already holds the max)
+  CK(cudaMemcpyAsync(m->khist, m->kap, (size_t)g.nvox * sizeof(R), cudaMemcpyDeviceToDevice, c->st), "commit");
+  CK(cudaStreamSynchronize(c->st), "synchronize");
+  return RVE_OK;
+}
+
+// ------------------------------------------------------------ L-BFGS
+// One load step by L-BFGS with the first-order incremental energy (Eq. (18))
+// in a backtracking Armijo line search (Nocedal & Wright Alg. 7.5 with the
+// two-loop recursion of Alg. 7.4; the paper's remark after Eq. (20)):
+// p = -H g; halve the step s = alpha p until
+// 1/2 (sigma + sigma(eps + s)) : s <= c1 sigma : s; eps += s; the pair
+// (s, y = g_new - g) is kept when s.y > 1e-12 |s| |y|, H0 = gamma I with
+// gamma = s.y / y.y of the newest pair (before any pair 1 / max(3 lam + 2 mu)).
+// Pairs are kept by pointer swaps: the accepted step (in d) and y (in r)
+// become the pair's fields and the evicted ones take over d and r.
+constexpr double kLbC1 = 1e-4;
+constexpr int kLbMaxBacktrack = 40;
+
+template <typename R>
+rve_status lbfgs_alloc(rve_ctx* c, int mem) {
+  Impl<R>* m = impl_of<R>(c);
+  if (m->lb_mem == mem) return RVE_OK;
+  for (int i = 0; i < kLbMaxMemory; ++i) {
+    if (m->lbS[i]) cudaFree(m->lbS[i]);
+    if (m->lbY[i]) cudaFree(m->lbY[i]);
+    m->lbS[i] = m->lbY[i] = nullptr;
+  }
+  m->lb_mem = 0;
+  const size_t nf = (size_t)c->g.ncomp * c->g.nvox * sizeof(R);
+  for (int i = 0; i < mem; ++i) {
+    CK(cudaMalloc(&m->lbS[i], nf), "L-BFGS pair allocation");
+    CK(cudaMalloc(&m->lbY[i], nf), "L-BFGS pair allocation");
+  }
+  if (!m->L) CK(cudaMalloc(&m->L, sizeof(LbScalars)), "L-BFGS scalar allocation");
+  if (!m->Lh) CK(cudaMallocHost(&m->Lh, sizeof(LbScalars)), "L-BFGS pinned allocation");
+  m->lb_mem = mem;
+  return RVE_OK;
+}
+
+template <typename R>
+rve_status lbfgs_step_impl(rve_ctx* c, const double dE[6], int mem, int max_iter, rve_step_report* rp) {
+  rve_status s = lbfgs_alloc<R>(c, mem);
+  if (s != RVE_OK) return s;
+  Impl<R>* m = impl_of<R>(c);
+  const GridDesc& g = c->g;
+  long long* nl = &c->launches;
+  const long long n = (long long)g.ncomp * g.nvox;
+  double* part = m->sw.partials;
+  std::memset(rp, 0, sizeof(*rp));
+  double cmax = 0.0;
+  for (int i = 0; i < m->mt.nphase; ++i)
+    cmax = std::max(cmax, 3.0 * (double)m->mt.lam[i] + 2.0 * (double)m->mt.mu[i]);
+  const double gamma0 = 1.0 / cmax;
+  CK(add_uniform<R>(g, m->eps, dE, c->st, nl), "load increment");
+  CK(trial_eval<R>(g, m->mt, m->eg, m->phase, m->eps, nullptr, m->khist, nullptr, nullptr, m->sig, m->D, m->kap,
+                   m->S, part, c->st, nl),
+     "stress");
+  if ((s = gradient<R>(c)) != RVE_OK) return s;
+  if ((s = read_scalars<R>(c)) != RVE_OK) return s;
+  double rel = c->Sh->sts > 0 ? std::sqrt(c->Sh->gg / c->Sh->sts) : 0.0;
+  std::vector<int> ord;  // pair slots, oldest first
+  double rho[kLbMaxMemory] = {};
+  double gamma = gamma0;
+  double alpha = 0.0;
+  // d = -H g by the two-loop recursion
+  auto direction = [&]() -> cudaError_t {
+    PassScope ps(&c->timer, c->st, PASS_CGVEC);
+    const int k = (int)ord.size();
+    if (k == 0) return lb_scale<R>(n, m->g, m->d, -gamma0, c->st, nl);
+    cudaError_t e = lb_dot<R>(n, m->lbS[ord[k - 1]], m->g, m->L, part, c->st, nl);
+    for (int j = k - 1; j >= 0 && e == cudaSuccess; --j) {
+      const int i = ord[j];
+      const R* w = j > 0 ? m->lbS[ord[j - 1]] : m->lbY[ord[0]];
+      e = lb_loop1<R>(n, j == k - 1 ? m->g : m->tmp, m->tmp, m->lbY[i], w, rho[i], i, m->L, part, c->st, nl);
+    }
+    for (int j = 0; j < k && e == cudaSuccess; ++j) {
+      const int i = ord[j];
+      const bool last = j == k - 1;
+      e = lb_loop2<R>(n, m->tmp, last ? m->d : m->tmp, m->lbS[i], last ? nullptr : m->lbY[ord[j + 1]], rho[i],
+                      j == 0 ? gamma : 1.0, last ? -1.0 : 1.0, i, m->L, part, c->st, nl);
+    }
+    return e;
+  };
+  auto trial = [&]() -> rve_status {
+    ++rp->cg_iters;
+    {
+      PassScope ps(&c->timer, c->st, PASS_TRIAL);
+      CK(trial_eval<R>(g, m->mt, m->eg, m->phase, m->eps, m->d, m->khist, m->sig, m->D, m->sig_t, m->D_t,
+                       m->kap_t, m->S, part, c->st, nl),
+         "trial stress");
+    }
+    rve_status t = read_scalars<R>(c);
+    if (t != RVE_OK) return t;
+    const DevScalars& h = *c->Sh;
+    if (!std::isfinite(h.sp) || !std::isfinite(h.stp) || !std::isfinite(h.sts))
+      return fail(c, RVE_ERR_NONFINITE, "non-finite trial state");
+    return RVE_OK;
+  };
+  bool failed = false;
+  while (rel > c->opts.eta_eq && rp->nr_iters < max_iter) {
+    rp->nr_iters++;
+    CK(direction(), "L-BFGS direction");
+    alpha = 1.0;
+    if ((s = trial()) != RVE_OK) return s;
+    if (!(c->Sh->sp < 0.0)) {
+      // not a descent direction (rounding at the floor): drop the pairs and
+      // take the scaled gradient step
+      ord.clear();
+      gamma = gamma0;
+      rp->boundary_hits++;
+      CK(direction(), "L-BFGS direction");
+      if ((s = trial()) != RVE_OK) return s;
+    }
+    bool ok = false;
+    for (int b = 0; b <= kLbMaxBacktrack; ++b) {
+      const double sp = c->Sh->sp, dW = 0.5 * (sp + c->Sh->stp);
+      if (dW <= kLbC1 * sp) {
+        ok = true;
+        break;
+      }
+      if (b == kLbMaxBacktrack) break;
+      alpha *= 0.5;
+      rp->rejected++;
+      CK(lb_scale<R>(n, m->d, m->d, 0.5, c->st, nl), "step halving");
+      if ((s = trial()) != RVE_OK) return s;
+    }
+    if (!ok) {
+      failed = true;
+      break;
+    }
+    const double pp = c->Sh->pp, sts = c->Sh->sts;
+    CK(axpy<R>(n, (R)1, m->d, m->eps, c->st, nl), "accept step");
+    std::swap(m->sig, m->sig_t);
+    std::swap(m->D, m->D_t);
+    std::swap(m->kap, m->kap_t);
+    CK(spectral_apply<R>(g, m->sw, m->mt, m->sig, m->phase, m->D, XIn::Plain, m->r, m->r, &m->S->gg, c->st, nl),
+       "gradient");
+    CK(lb_pair<R>(n, m->d, m->g, m->r, m->L, part, c->st, nl), "pair update");
+    CK(cudaMemcpyAsync(m->Lh, m->L, sizeof(LbScalars), cudaMemcpyDeviceToHost, c->st), "read L-BFGS scalars");
+    if ((s = read_scalars<R>(c)) != RVE_OK) return s;
+    const double sy = m->Lh->sy, yy = m->Lh->yy;
+    if (!std::isfinite(sy) || !std::isfinite(yy) || !std::isfinite(c->Sh->gg))
+      return fail(c, RVE_ERR_NONFINITE, "non-finite gradient");
+    if (sy > 1e-12 * std::sqrt(pp) * std::sqrt(yy)) {
+      int slot;
+      if ((int)ord.size() < mem) {
+        slot = 0;
+        while (std::find(ord.begin(), ord.end(), slot) != ord.end()) ++slot;
+      } else {
+        slot = ord.front();
+        ord.erase(ord.begin());
+      }
+      std::swap(m->lbS[slot], m->d);
+      std::swap(m->lbY[slot], m->r);
+      rho[slot] = 1.0 / sy;
+      gamma = sy / yy;
+      ord.push_back(slot);
+    } else {
+      rp->restarts++;
+    }
+    rel = sts > 0 ? std::sqrt(c->Sh->gg / sts) : 0.0;
+  }
+  CK(field_means<R>(g, m->sig, m->eps, m->S, part, c->st, nl), "means");
+  if ((s = read_scalars<R>(c)) != RVE_OK) return s;
+  for (int i = 0; i < 6; ++i) {
+    rp->mean_stress[i] = c->Sh->msig[i] / (double)g.nvox;
+    rp->mean_strain[i] = c->Sh->meps[i] / (double)g.nvox;
+  }
+  rp->rel_residual = rel;
+  rp->R = alpha;
+  const bool converged = !failed && rel <= c->opts.eta_eq;
+  rp->converged = converged ? 1 : 0;
+  if (!converged)
+    return fail(c, RVE_ERR_NOT_CONVERGED,
+                failed ? "L-BFGS line search failed" : "L-BFGS load step did not converge within max_iter");
   CK(cudaMemcpyAsync(m->khist, m->kap, (size_t)g.nvox * sizeof(R), cudaMemcpyDeviceToDevice, c->st), "commit");
   CK(cudaStreamSynchronize(c->st), "synchronize");
   return RVE_OK;
@@ -547,6 +736,20 @@ rve_status rve_solve_step(rve_t c, const double dE[6], const uint8_t fm[6], cons
     if (s != RVE_OK) return s;
   }
   return DISPATCH(c, solve_step_impl, dE, init, rep);
+}
+
+rve_status rve_solve_step_lbfgs(rve_t c, const double dE[6], const uint8_t fm[6], int memory, int max_iter,
+                                rve_step_report* rep) {
+  if (!c) return RVE_ERR_ARG;
+  if (!dE) return fail(c, RVE_ERR_ARG, "dE is NULL");
+  if (memory < 1 || memory > kLbMaxMemory) return fail(c, RVE_ERR_ARG, "memory must be in [1, 16]");
+  if (max_iter < 1) return fail(c, RVE_ERR_ARG, "max_iter must be >= 1");
+  if (fm) {
+    rve_status s = rve_set_free_mask(c, fm);
+    if (s != RVE_OK) return s;
+  }
+  rve_step_report local{};
+  return DISPATCH(c, lbfgs_step_impl, dE, memory, max_iter, rep ? rep : &local);
 }
 
 rve_status rve_pass_timing(rve_t c, int enable) {

@@ -132,6 +132,15 @@ class RVESolver:
         d["status"] = st
         return d
 
+    def solve_step_lbfgs(self, dE, free_mask=None, memory=5, max_iter=500, raise_on_error=True):
+        """One load step by L-BFGS with the first-order incremental energy in
+        its line search (report: nr_iters = iterations, cg_iters = line-search
+        trials, rejected = step halvings, restarts = skipped pairs)."""
+        st, rep = B.rve_solve_step_lbfgs(self.h, dE, free_mask, memory, max_iter, raise_on_error)
+        d = _report_dict(rep)
+        d["status"] = st
+        return d
+
     @property
     def hv_count(self):
         return B.rve_hv_count(self.h)

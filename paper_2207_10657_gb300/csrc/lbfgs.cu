@@ -1,7 +1,8 @@
-// L-BFGS vector kernels (Nocedal & Wright Alg. 7.4 / 7.5; the paper's remark
-// after Eq. (20) that the first-order incremental energy makes quasi-Newton
-// methods usable).  Each pass is a grid-stride stream over 4-wide vectors;
-// sums are Neumaier-compensated per thread and FP64 across threads.
+// L-BFGS vector kernels (Nocedal & Wright Alg. 7.5 with the compact
+// representation of the inverse Hessian; the paper's remark after Eq. (20)
+// that the first-order incremental energy makes quasi-Newton methods
+// usable).  Each pass is a grid-stride stream over 4-wide vectors; sums are
+// Neumaier-compensated per thread and FP64 across threads.
 #include "hv_passes.cuh"
 #include "lbfgs.cuh"
 
@@ -38,62 +39,115 @@ __device__ __forceinline__ void block_partials(KSum<R> (&acc)[NS], double* part)
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kLThreads) k_lb_dot(long long n4, const R* __restrict__ x, const R* __restrict__ y,
-                                                      double* __restrict__ part) {
-  KSum<R> acc[1];
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
-    W4<R> a = ld4(x, i), b = ld4(y, i);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) acc[0].add(el<R>(a, e) * el<R>(b, e));
-  }
-  block_partials<R, 1>(acc, part);
-}
+struct LbGroup {
+  const R* s[kLbGroup];
+  const R* y[kLbGroup];
+};
 
-template <typename R>
+// Pass A over one group of G pairs: s_i . g, y_i . g and, with NEWP, s_i . yn
+// and y_i . yn (yn the newest pair's y).
+template <typename R, int G, bool NEWP>
 __global__ void __launch_bounds__(kLThreads)
-    k_lb_loop1(long long n4, const R* src, R* q, const R* __restrict__ y, const R* __restrict__ w, double rho, int i,
-               LbScalars* L, double* __restrict__ part) {
-  const double a = rho * L->sum;
-  const R ar = (R)a;
-  KSum<R> acc[1];
+    k_lb_dots(long long n4, const R* __restrict__ g, const LbGroup<R> P, const R* __restrict__ yn,
+              double* __restrict__ part) {
+  KSum<R> acc[4 * G];
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n4; k += (long long)gridDim.x * blockDim.x) {
-    W4<R> v = ld4(src, k), yy = ld4(y, k);
+    W4<R> g4 = ld4(g, k), n4v;
+    if constexpr (NEWP) n4v = ld4(yn, k);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) el<R>(v, e) -= ar * el<R>(yy, e);
-    st4(q, k, v);
-    if (w) {
-      W4<R> ww = ld4(w, k);
+    for (int i = 0; i < G; ++i) {
+      W4<R> s4 = ld4(P.s[i], k), y4 = ld4(P.y[i], k);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) acc[0].add(el<R>(ww, e) * el<R>(v, e));
+      for (int e = 0; e < 4; ++e) {
+        acc[i].add(el<R>(s4, e) * el<R>(g4, e));
+        acc[G + i].add(el<R>(y4, e) * el<R>(g4, e));
+        if constexpr (NEWP) {
+          acc[2 * G + i].add(el<R>(s4, e) * el<R>(n4v, e));
+          acc[3 * G + i].add(el<R>(y4, e) * el<R>(n4v, e));
+        }
+      }
     }
   }
-  block_partials<R, 1>(acc, part);
-  // every thread has read L->sum before any block can finish; the block that
-  // stores a_i does so after its own reads
-  if (blockIdx.x == 0 && threadIdx.x == 0) L->a[i] = a;
+  block_partials<R, 4 * G>(acc, part);
 }
 
-template <typename R>
+struct LbCoefArgs {
+  int k, new_pair;
+  int slot[kLbMaxMemory];
+  double gamma;
+};
+
+// One thread: new entries of S^T Y and Y^T Y, then the two triangular solves
+// of the compact representation and the coefficients of pass C.
+__global__ void k_lb_coef(LbScalars* L, const LbCoefArgs A) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const int k = A.k;
+  double a[kLbMaxMemory], c[kLbMaxMemory], u[kLbMaxMemory], t[kLbMaxMemory], p[kLbMaxMemory];
+  for (int j = 0; j < k; ++j) {
+    const int q = j / kLbGroup, i = j % kLbGroup;
+    const int G = min(kLbGroup, k - q * kLbGroup);
+    a[j] = L->gsum[q][i];
+    c[j] = L->gsum[q][G + i];
+    if (A.new_pair) {
+      const int sj = A.slot[j], sn = A.slot[k - 1];
+      L->SY[sj][sn] = L->gsum[q][2 * G + i];
+      L->YY[sj][sn] = L->gsum[q][3 * G + i];
+      L->YY[sn][sj] = L->gsum[q][3 * G + i];
+    }
+  }
+  // R_ij = s_i . y_j (i <= j) in ring order; u = R^-1 a
+  for (int i = k - 1; i >= 0; --i) {
+    double v = a[i];
+    for (int j = i + 1; j < k; ++j) v -= L->SY[A.slot[i]][A.slot[j]] * u[j];
+    u[i] = v / L->SY[A.slot[i]][A.slot[i]];
+  }
+  // t = (D + gamma Y^T Y) u - gamma c; p = R^-T t
+  for (int i = 0; i < k; ++i) {
+    double v = L->SY[A.slot[i]][A.slot[i]] * u[i] - A.gamma * c[i];
+    for (int j = 0; j < k; ++j) v += A.gamma * L->YY[A.slot[i]][A.slot[j]] * u[j];
+    t[i] = v;
+  }
+  for (int i = 0; i < k; ++i) {
+    double v = t[i];
+    for (int j = 0; j < i; ++j) v -= L->SY[A.slot[j]][A.slot[i]] * p[j];
+    p[i] = v / L->SY[A.slot[i]][A.slot[i]];
+  }
+  for (int j = 0; j < k; ++j) {
+    L->cS[j] = -p[j];
+    L->cY[j] = A.gamma * u[j];
+  }
+}
+
+// Pass C over one group: d = cg g + sum cS_i s_i + cY_i y_i (FIRST), or
+// d += the group's terms.
+template <typename R, int G, bool FIRST>
 __global__ void __launch_bounds__(kLThreads)
-    k_lb_loop2(long long n4, const R* src, R* out, const R* __restrict__ s, const R* __restrict__ w, double rho,
-               double f, double sgn, int i, const LbScalars* __restrict__ L, double* __restrict__ part) {
-  const double b = rho * f * L->sum;
-  const R c = (R)(L->a[i] - b), fr = (R)f, sr = (R)sgn;
-  KSum<R> acc[1];
+    k_lb_combine(long long n4, const R* __restrict__ g, const LbGroup<R> P, const double* __restrict__ cS,
+                 const double* __restrict__ cY, double cg, R* d) {
+  R a[G], b[G];
+#pragma unroll
+  for (int i = 0; i < G; ++i) {
+    a[i] = (R)cS[i];
+    b[i] = (R)cY[i];
+  }
+  const R cgr = (R)cg;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n4; k += (long long)gridDim.x * blockDim.x) {
-    W4<R> v = ld4(src, k), ss = ld4(s, k), o;
+    W4<R> v;
+    if constexpr (FIRST) {
+      v = ld4(g, k);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) el<R>(v, e) = fr * el<R>(v, e) + c * el<R>(ss, e);
-    if (w) {
-      W4<R> ww = ld4(w, k);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[0].add(el<R>(ww, e) * el<R>(v, e));
+      for (int e = 0; e < 4; ++e) el<R>(v, e) *= cgr;
+    } else {
+      v = ld4(d, k);
     }
 #pragma unroll
-    for (int e = 0; e < 4; ++e) el<R>(o, e) = sr * el<R>(v, e);
-    st4(out, k, o);
+    for (int i = 0; i < G; ++i) {
+      W4<R> s4 = ld4(P.s[i], k), y4 = ld4(P.y[i], k);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) el<R>(v, e) += a[i] * el<R>(s4, e) + b[i] * el<R>(y4, e);
+    }
+    st4(d, k, v);
   }
-  block_partials<R, 1>(acc, part);
 }
 
 template <typename R>
@@ -127,34 +181,80 @@ __global__ void __launch_bounds__(kLThreads)
 
 }  // namespace
 
+template <typename R, int G>
+static cudaError_t dots_g(long long n4, const R* g, const LbGroup<R>& P, const R* yn, double* part,
+                         cudaStream_t st) {
+  if (yn) k_lb_dots<R, G, true><<<kLBlocks, kLThreads, 0, st>>>(n4, g, P, yn, part);
+  else k_lb_dots<R, G, false><<<kLBlocks, kLThreads, 0, st>>>(n4, g, P, yn, part);
+  return cudaGetLastError();
+}
+
+template <typename R, int G>
+static cudaError_t combine_g(long long n4, const R* g, const LbGroup<R>& P, const double* cS, const double* cY,
+                             double cg, bool first, R* d, cudaStream_t st) {
+  if (first) k_lb_combine<R, G, true><<<kLBlocks, kLThreads, 0, st>>>(n4, g, P, cS, cY, cg, d);
+  else k_lb_combine<R, G, false><<<kLBlocks, kLThreads, 0, st>>>(n4, g, P, cS, cY, cg, d);
+  return cudaGetLastError();
+}
+
+#define RVE_LB_GSWITCH(G_, CALL) \
+  switch (G_) {                  \
+    case 1: e = CALL(1); break;  \
+    case 2: e = CALL(2); break;  \
+    case 3: e = CALL(3); break;  \
+    case 4: e = CALL(4); break;  \
+    case 5: e = CALL(5); break;  \
+    case 6: e = CALL(6); break;  \
+    case 7: e = CALL(7); break;  \
+    default: e = CALL(8); break; \
+  }
+
 template <typename R>
-cudaError_t lb_dot(long long n, const R* x, const R* y, LbScalars* L, double* part, cudaStream_t st,
-                   long long* nl) {
-  k_lb_dot<R><<<kLBlocks, kLThreads, 0, st>>>(n / 4, x, y, part);
-  ++*nl;
-  cudaError_t e = cudaGetLastError();
+cudaError_t lb_direction(long long n, const R* g, const LbRing<R>& ring, bool new_pair, double gamma, R* d,
+                         LbScalars* L, double* part, cudaStream_t st, long long* nl) {
+  const int k = ring.k;
+  const long long n4 = n / 4;
+  if (k < 1 || k > kLbMaxMemory) return cudaErrorInvalidValue;
+  const int ngrp = (k + kLbGroup - 1) / kLbGroup;
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < ngrp && e == cudaSuccess; ++q) {
+    const int G = min(kLbGroup, k - q * kLbGroup);
+    LbGroup<R> P{};
+    for (int i = 0; i < G; ++i) {
+      P.s[i] = ring.s[q * kLbGroup + i];
+      P.y[i] = ring.y[q * kLbGroup + i];
+    }
+    const R* yn = new_pair ? ring.y[k - 1] : nullptr;
+#define RVE_LB_DOTS(G_) dots_g<R, G_>(n4, g, P, yn, part, st)
+    RVE_LB_GSWITCH(G, RVE_LB_DOTS)
+#undef RVE_LB_DOTS
+    ++*nl;
+    if (e == cudaSuccess) e = reduce_partials(part, kLBlocks, 4 * G, &L->gsum[q][0], st, nl);
+  }
   if (e != cudaSuccess) return e;
-  return reduce_partials(part, kLBlocks, 1, &L->sum, st, nl);
-}
-
-template <typename R>
-cudaError_t lb_loop1(long long n, const R* src, R* q, const R* y, const R* w, double rho, int i, LbScalars* L,
-                     double* part, cudaStream_t st, long long* nl) {
-  k_lb_loop1<R><<<kLBlocks, kLThreads, 0, st>>>(n / 4, src, q, y, w, rho, i, L, part);
+  LbCoefArgs A{};
+  A.k = k;
+  A.new_pair = new_pair ? 1 : 0;
+  A.gamma = gamma;
+  for (int j = 0; j < k; ++j) A.slot[j] = ring.slot[j];
+  k_lb_coef<<<1, 1, 0, st>>>(L, A);
   ++*nl;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || !w) return e;
-  return reduce_partials(part, kLBlocks, 1, &L->sum, st, nl);
-}
-
-template <typename R>
-cudaError_t lb_loop2(long long n, const R* src, R* out, const R* s, const R* w, double rho, double f, double sgn,
-                     int i, LbScalars* L, double* part, cudaStream_t st, long long* nl) {
-  k_lb_loop2<R><<<kLBlocks, kLThreads, 0, st>>>(n / 4, src, out, s, w, rho, f, sgn, i, L, part);
-  ++*nl;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || !w) return e;
-  return reduce_partials(part, kLBlocks, 1, &L->sum, st, nl);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int q = 0; q < ngrp && e == cudaSuccess; ++q) {
+    const int G = min(kLbGroup, k - q * kLbGroup);
+    LbGroup<R> P{};
+    for (int i = 0; i < G; ++i) {
+      P.s[i] = ring.s[q * kLbGroup + i];
+      P.y[i] = ring.y[q * kLbGroup + i];
+    }
+    const double* cS = &L->cS[q * kLbGroup];
+    const double* cY = &L->cY[q * kLbGroup];
+#define RVE_LB_COMB(G_) combine_g<R, G_>(n4, g, P, cS, cY, -gamma, q == 0, d, st)
+    RVE_LB_GSWITCH(G, RVE_LB_COMB)
+#undef RVE_LB_COMB
+    ++*nl;
+  }
+  return e;
 }
 
 template <typename R>
@@ -174,13 +274,10 @@ cudaError_t lb_pair(long long n, const R* s, R* g, R* gnew, LbScalars* L, double
   return reduce_partials(part, kLBlocks, 2, &L->sy, st, nl);
 }
 
-#define RVE_LB_INST(R)                                                                                           \
-  template cudaError_t lb_dot<R>(long long, const R*, const R*, LbScalars*, double*, cudaStream_t, long long*); \
-  template cudaError_t lb_loop1<R>(long long, const R*, R*, const R*, const R*, double, int, LbScalars*,       \
-                                   double*, cudaStream_t, long long*);                                         \
-  template cudaError_t lb_loop2<R>(long long, const R*, R*, const R*, const R*, double, double, double, int,   \
-                                   LbScalars*, double*, cudaStream_t, long long*);                             \
-  template cudaError_t lb_scale<R>(long long, const R*, R*, double, cudaStream_t, long long*);                 \
+#define RVE_LB_INST(R)                                                                                         \
+  template cudaError_t lb_direction<R>(long long, const R*, const LbRing<R>&, bool, double, R*, LbScalars*,   \
+                                       double*, cudaStream_t, long long*);                                    \
+  template cudaError_t lb_scale<R>(long long, const R*, R*, double, cudaStream_t, long long*);                \
   template cudaError_t lb_pair<R>(long long, const R*, R*, R*, LbScalars*, double*, cudaStream_t, long long*);
 
 RVE_LB_INST(float)

@@ -342,8 +342,9 @@ rve_status solve_step_impl(rve_ctx* c, const double dE[6], const void* init, rve
 
 // ------------------------------------------------------------ L-BFGS
 // One load step by L-BFGS with the first-order incremental energy (Eq. (18))
-// in a backtracking Armijo line search (Nocedal & Wright Alg. 7.5 with the
-// two-loop recursion of Alg. 7.4; the paper's remark after Eq. (20)):
+// in a backtracking Armijo line search (Nocedal & Wright Alg. 7.5, the
+// direction from the compact representation of the inverse Hessian, equal to
+// the two-loop recursion of Alg. 7.4; the paper's remark after Eq. (20)):
 // p = -H g; halve the step s = alpha p until
 // 1/2 (sigma + sigma(eps + s)) : s <= c1 sigma : s; eps += s; the pair
 // (s, y = g_new - g) is kept when s.y > 1e-12 |s| |y|, H0 = gamma I with
@@ -396,26 +397,23 @@ rve_status lbfgs_step_impl(rve_ctx* c, const double dE[6], int mem, int max_iter
   if ((s = read_scalars<R>(c)) != RVE_OK) return s;
   double rel = c->Sh->sts > 0 ? std::sqrt(c->Sh->gg / c->Sh->sts) : 0.0;
   std::vector<int> ord;  // pair slots, oldest first
-  double rho[kLbMaxMemory] = {};
+  bool new_pair = false;  // a pair entered since the last direction
   double gamma = gamma0;
   double alpha = 0.0;
-  // d = -H g by the two-loop recursion
+  // d = -H g (compact representation of the L-BFGS inverse Hessian)
   auto direction = [&]() -> cudaError_t {
     PassScope ps(&c->timer, c->st, PASS_CGVEC);
     const int k = (int)ord.size();
     if (k == 0) return lb_scale<R>(n, m->g, m->d, -gamma0, c->st, nl);
-    cudaError_t e = lb_dot<R>(n, m->lbS[ord[k - 1]], m->g, m->L, part, c->st, nl);
-    for (int j = k - 1; j >= 0 && e == cudaSuccess; --j) {
-      const int i = ord[j];
-      const R* w = j > 0 ? m->lbS[ord[j - 1]] : m->lbY[ord[0]];
-      e = lb_loop1<R>(n, j == k - 1 ? m->g : m->tmp, m->tmp, m->lbY[i], w, rho[i], i, m->L, part, c->st, nl);
+    LbRing<R> ring{};
+    ring.k = k;
+    for (int j = 0; j < k; ++j) {
+      ring.slot[j] = ord[j];
+      ring.s[j] = m->lbS[ord[j]];
+      ring.y[j] = m->lbY[ord[j]];
     }
-    for (int j = 0; j < k && e == cudaSuccess; ++j) {
-      const int i = ord[j];
-      const bool last = j == k - 1;
-      e = lb_loop2<R>(n, m->tmp, last ? m->d : m->tmp, m->lbS[i], last ? nullptr : m->lbY[ord[j + 1]], rho[i],
-                      j == 0 ? gamma : 1.0, last ? -1.0 : 1.0, i, m->L, part, c->st, nl);
-    }
+    const cudaError_t e = lb_direction<R>(n, m->g, ring, new_pair, gamma, m->d, m->L, part, c->st, nl);
+    new_pair = false;
     return e;
   };
   auto trial = [&]() -> rve_status {
@@ -443,6 +441,7 @@ rve_status lbfgs_step_impl(rve_ctx* c, const double dE[6], int mem, int max_iter
       // not a descent direction (rounding at the floor): drop the pairs and
       // take the scaled gradient step
       ord.clear();
+      new_pair = false;
       gamma = gamma0;
       rp->boundary_hits++;
       CK(direction(), "L-BFGS direction");
@@ -489,9 +488,9 @@ rve_status lbfgs_step_impl(rve_ctx* c, const double dE[6], int mem, int max_iter
       }
       std::swap(m->lbS[slot], m->d);
       std::swap(m->lbY[slot], m->r);
-      rho[slot] = 1.0 / sy;
       gamma = sy / yy;
       ord.push_back(slot);
+      new_pair = true;
     } else {
       rp->restarts++;
     }

@@ -3,6 +3,8 @@
 // that the first-order incremental energy makes quasi-Newton methods
 // usable).  Each pass is a grid-stride stream over 4-wide vectors; sums are
 // Neumaier-compensated per thread and FP64 across threads.
+#include <algorithm>
+
 #include "hv_passes.cuh"
 #include "lbfgs.cuh"
 
@@ -181,19 +183,39 @@ __global__ void __launch_bounds__(kLThreads)
 
 }  // namespace
 
+// One full wave: the SM count times the blocks of `kernel` resident per SM
+// (the pass kernels of large groups hold many accumulators, so fewer blocks
+// fit than the default grid assumes and a second, partial wave would idle
+// most of the GPU), capped so that ns partial sums per block fit the
+// partial-sum buffer.
+template <typename K>
+static int full_wave(K kernel, int ns) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+      cudaSuccess || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kLThreads, 0) != cudaSuccess ||
+      per < 1 || sms < 1)
+    return kLBlocks;
+  return std::max(1, std::min(sms * per, 32768 / std::max(ns, 1)));
+}
+
 template <typename R, int G>
 static cudaError_t dots_g(long long n4, const R* g, const LbGroup<R>& P, const R* yn, double* part,
-                         cudaStream_t st) {
-  if (yn) k_lb_dots<R, G, true><<<kLBlocks, kLThreads, 0, st>>>(n4, g, P, yn, part);
-  else k_lb_dots<R, G, false><<<kLBlocks, kLThreads, 0, st>>>(n4, g, P, yn, part);
+                          cudaStream_t st, int* nblocks) {
+  static const int bt = full_wave(k_lb_dots<R, G, true>, 4 * G);
+  static const int bf = full_wave(k_lb_dots<R, G, false>, 4 * G);
+  if (yn) k_lb_dots<R, G, true><<<bt, kLThreads, 0, st>>>(n4, g, P, yn, part);
+  else k_lb_dots<R, G, false><<<bf, kLThreads, 0, st>>>(n4, g, P, yn, part);
+  *nblocks = yn ? bt : bf;
   return cudaGetLastError();
 }
 
 template <typename R, int G>
 static cudaError_t combine_g(long long n4, const R* g, const LbGroup<R>& P, const double* cS, const double* cY,
                              double cg, bool first, R* d, cudaStream_t st) {
-  if (first) k_lb_combine<R, G, true><<<kLBlocks, kLThreads, 0, st>>>(n4, g, P, cS, cY, cg, d);
-  else k_lb_combine<R, G, false><<<kLBlocks, kLThreads, 0, st>>>(n4, g, P, cS, cY, cg, d);
+  static const int bt = full_wave(k_lb_combine<R, G, true>, 0);
+  static const int bf = full_wave(k_lb_combine<R, G, false>, 0);
+  if (first) k_lb_combine<R, G, true><<<bt, kLThreads, 0, st>>>(n4, g, P, cS, cY, cg, d);
+  else k_lb_combine<R, G, false><<<bf, kLThreads, 0, st>>>(n4, g, P, cS, cY, cg, d);
   return cudaGetLastError();
 }
 
@@ -225,11 +247,12 @@ cudaError_t lb_direction(long long n, const R* g, const LbRing<R>& ring, bool ne
       P.y[i] = ring.y[q * kLbGroup + i];
     }
     const R* yn = new_pair ? ring.y[k - 1] : nullptr;
-#define RVE_LB_DOTS(G_) dots_g<R, G_>(n4, g, P, yn, part, st)
+    int nb = kLBlocks;
+#define RVE_LB_DOTS(G_) dots_g<R, G_>(n4, g, P, yn, part, st, &nb)
     RVE_LB_GSWITCH(G, RVE_LB_DOTS)
 #undef RVE_LB_DOTS
     ++*nl;
-    if (e == cudaSuccess) e = reduce_partials(part, kLBlocks, 4 * G, &L->gsum[q][0], st, nl);
+    if (e == cudaSuccess) e = reduce_partials(part, nb, 4 * G, &L->gsum[q][0], st, nl);
   }
   if (e != cudaSuccess) return e;
   LbCoefArgs A{};

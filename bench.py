@@ -122,12 +122,13 @@ def _kernel_hash():
     """Hash of the sources of the kernels whose DRAM counters
     profiles/traffic.json holds (spectral passes, constitutive and CG vector
     kernels).  The network, the batched solver, the allocation-free
-    projection, the L-BFGS vector kernels and the host-side control loop
+    projection, the L-BFGS and homogenisation kernels and the host-side control loop
     (rve_api.cu: entry points and one-thread scalar kernels) live in files of
     their own and do not enter it."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2207_10657_gb300", "csrc")
-    skip = {"fno.cu", "batch.cu", "noalloc.cu", "lbfgs.cu", "lbfgs.cuh", "rve_api.cu"}
+    skip = {"fno.cu", "batch.cu", "noalloc.cu", "lbfgs.cu", "lbfgs.cuh", "homogenize.cu", "homogenize.cuh",
+            "rve_api.cu"}
     for fn in sorted(os.listdir(csrc)):
         if fn.endswith((".cu", ".cuh")) and fn not in skip:
             with open(os.path.join(csrc, fn), "rb") as f:

@@ -197,6 +197,25 @@ rve_status rve_solve_step(rve_t, const double dE_host[6], const uint8_t free_mas
 rve_status rve_solve_step_lbfgs(rve_t, const double dE_host[6], const uint8_t free_mask_host[6],
                                 int memory, int max_iter, rve_step_report* rep_host);
 
+/* Effective (homogenised) secant stiffness of the cell at the current damage
+ * field D (the state's, or the one set by rve_set_damage), for the
+ * stiffness-loss measure ||C_bar|| / ||C_bar_0|| of the ASR example
+ * (Sec. 3.3).  For every Mandel unit mean strain e_j, with every mean
+ * component strain-controlled, the fluctuation x_j solving
+ * G : (1-D) C : (e_j + x_j) = 0 is found by Steihaug CG without a radius
+ * (Algorithm 1 on the product of Eq. (8)) to |r| <= tol |G:(1-D)C:e_j|;
+ * C_bar column j = <(1-D) C : (e_j + x_j)>.
+ *  tol             relative CG tolerance, in (0, 1)
+ *  max_cg          CG iteration cap per column (>= 1)
+ *  Cbar_host       ncomp x ncomp doubles, row-major, Mandel (written)
+ *  cg_iters_host   total CG iterations (may be NULL)
+ * The state, the free mask, the trust radius and the options are left as
+ * they were; the Hessian-vector counter counts the products.  Synchronises
+ * the stream.  RVE_ERR_ARG on bad arguments; RVE_ERR_NOT_CONVERGED when a
+ * column's CG reaches max_cg (or meets zero curvature on a fully damaged
+ * cell). */
+rve_status rve_effective_stiffness(rve_t, double tol, int max_cg, double* Cbar_host, int* cg_iters_host);
+
 /* Per-pass device timing, for benchmarks (not part of the method).
  * Pass ids: 0 x-forward FFT with the fused tangent, 1 y-forward FFT,
  * 2 z-FFT + projection + inverse z-FFT, 3 y-inverse FFT, 4 x-inverse FFT,

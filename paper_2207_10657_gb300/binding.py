@@ -64,6 +64,8 @@ _SIGS = [
     ("rve_solve_step_lbfgs", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                             ctypes.POINTER(rve_step_report)]),
+    ("rve_effective_stiffness", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     ("rve_pass_timing", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("rve_pass_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
@@ -228,6 +230,14 @@ def rve_solve_step_lbfgs(h, dE, free_mask=None, memory=5, max_iter=500, raise_on
     if raise_on_error:
         check(st, h)
     return st, rep
+
+
+def rve_effective_stiffness(h, ncomp, tol=1e-6, max_cg=2000):
+    """(C_bar as ncomp rows of ncomp floats, total CG iterations)."""
+    out = (ctypes.c_double * (ncomp * ncomp))()
+    it = ctypes.c_int(0)
+    check(lib().rve_effective_stiffness(h, float(tol), int(max_cg), out, ctypes.byref(it)), h)
+    return [list(out[i * ncomp:(i + 1) * ncomp]) for i in range(ncomp)], it.value
 
 
 PASS_NAMES = ["xfwd_tangent", "y_fwd", "z_proj", "y_inv", "x_inv", "y_proj_2d", "trial", "cg_vec"]

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/rve.h"
+#include "homogenize.cuh"
 #include "hv_passes.cuh"
 #include "lbfgs.cuh"
 #include "solver_kernels.cuh"
@@ -514,6 +515,68 @@ rve_status lbfgs_step_impl(rve_ctx* c, const double dE[6], int mem, int max_iter
   return RVE_OK;
 }
 
+// ------------------------------------------------------ homogenisation
+// Effective secant stiffness at the frozen damage field: for every Mandel
+// unit mean strain e_j (all mean components strain-controlled), the
+// fluctuation x_j solving G:B:(e_j + x_j) = 0 by Steihaug CG without a
+// radius (Algorithm 1 on the Hessian-vector product of Eq. (8)); column j
+// is <(1 - D) C : (e_j + x_j)>.
+template <typename R>
+rve_status stiffness_impl(rve_ctx* c, double tol, int max_cg, double* Cbar, int* cg_total) {
+  Impl<R>* m = impl_of<R>(c);
+  const GridDesc& g = c->g;
+  long long* nl = &c->launches;
+  // the CG runs under the load-step machinery with its radius, tolerance and
+  // mask replaced; everything is put back before returning
+  const double R0 = c->R, Rm = c->Rmax;
+  const rve_solver_opts opts0 = c->opts;
+  const unsigned fm0 = m->sw.free_mask;
+  c->R = c->Rmax = 1e300;
+  c->opts.eta_cg = tol;
+  c->opts.max_cg = max_cg;
+  m->sw.free_mask = 0;
+  auto restore = [&]() {
+    c->R = R0;
+    c->Rmax = Rm;
+    c->opts = opts0;
+    m->sw.free_mask = fm0;
+  };
+  rve_status s = RVE_OK;
+  rve_step_report rep{};
+  for (int j = 0; j < g.ncomp && s == RVE_OK; ++j) {
+    double e[6] = {0, 0, 0, 0, 0, 0};
+    e[j] = 1.0;
+    cudaError_t ce = cudaMemsetAsync(m->tmp, 0, (size_t)g.ncomp * g.nvox * sizeof(R), c->st);
+    if (ce == cudaSuccess) ce = add_uniform<R>(g, m->tmp, e, c->st, nl);
+    if (ce == cudaSuccess)
+      ce = spectral_apply<R>(g, m->sw, m->mt, m->tmp, m->phase, m->D, XIn::Tangent, m->g, m->g, &m->S->gg, c->st,
+                             nl);
+    if (ce != cudaSuccess) {
+      s = cuda_fail(c, ce, "stiffness right-hand side");
+      break;
+    }
+    if ((s = steihaug<R>(c, &rep)) != RVE_OK) break;
+    const int st = c->Sh->status;
+    if (st != CG_CONVERGED && st != CG_ZERO) {
+      s = fail(c, RVE_ERR_NOT_CONVERGED, "effective stiffness: CG did not reach the tolerance within max_cg");
+      break;
+    }
+    // z = x_j (zero when the right-hand side vanishes: cg_init clears it)
+    ce = add_uniform<R>(g, m->z, e, c->st, nl);
+    if (ce == cudaSuccess)
+      ce = tangent_sum<R>(g, m->mt, m->phase, m->D, m->z, &m->S->msig[0], m->sw.partials, c->st, nl);
+    if (ce != cudaSuccess) {
+      s = cuda_fail(c, ce, "stiffness column");
+      break;
+    }
+    if ((s = read_scalars<R>(c)) != RVE_OK) break;
+    for (int i = 0; i < g.ncomp; ++i) Cbar[i * g.ncomp + j] = c->Sh->msig[i] / (double)g.nvox;
+  }
+  if (cg_total) *cg_total = rep.cg_iters;
+  restore();
+  return s;
+}
+
 template <typename R>
 rve_status set_state_impl(rve_ctx* c, const void* strain, const void* khist) {
   Impl<R>* m = impl_of<R>(c);
@@ -749,6 +812,14 @@ rve_status rve_solve_step_lbfgs(rve_t c, const double dE[6], const uint8_t fm[6]
   }
   rve_step_report local{};
   return DISPATCH(c, lbfgs_step_impl, dE, memory, max_iter, rep ? rep : &local);
+}
+
+rve_status rve_effective_stiffness(rve_t c, double tol, int max_cg, double* Cbar, int* cg_iters) {
+  if (!c) return RVE_ERR_ARG;
+  if (!Cbar) return fail(c, RVE_ERR_ARG, "Cbar is NULL");
+  if (!(tol > 0.0 && tol < 1.0)) return fail(c, RVE_ERR_ARG, "tol must be in (0, 1)");
+  if (max_cg < 1) return fail(c, RVE_ERR_ARG, "max_cg must be >= 1");
+  return DISPATCH(c, stiffness_impl, tol, max_cg, Cbar, cg_iters);
 }
 
 rve_status rve_pass_timing(rve_t c, int enable) {

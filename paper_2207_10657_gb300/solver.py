@@ -141,6 +141,11 @@ class RVESolver:
         d["status"] = st
         return d
 
+    def effective_stiffness(self, tol=1e-6, max_cg=2000):
+        """Effective secant stiffness (ncomp x ncomp Mandel, nested lists) at
+        the current damage field, and the CG iterations it took."""
+        return B.rve_effective_stiffness(self.h, self.ncomp, tol, max_cg)
+
     @property
     def hv_count(self):
         return B.rve_hv_count(self.h)

@@ -59,23 +59,14 @@ __global__ void __launch_bounds__(kLThreads)
 #pragma unroll
     for (int i = 0; i < G; ++i) {
       W4<R> s4 = ld4(P.s[i], k), y4 = ld4(P.y[i], k);
-      // the four products of a vector are summed plainly, the vector sums
-      // with compensation: a quarter of the compensated additions
-      R sg = 0, yg = 0, sn = 0, yn2 = 0;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        sg += el<R>(s4, e) * el<R>(g4, e);
-        yg += el<R>(y4, e) * el<R>(g4, e);
+        acc[i].add(el<R>(s4, e) * el<R>(g4, e));
+        acc[G + i].add(el<R>(y4, e) * el<R>(g4, e));
         if constexpr (NEWP) {
-          sn += el<R>(s4, e) * el<R>(n4v, e);
-          yn2 += el<R>(y4, e) * el<R>(n4v, e);
+          acc[2 * G + i].add(el<R>(s4, e) * el<R>(n4v, e));
+          acc[3 * G + i].add(el<R>(y4, e) * el<R>(n4v, e));
         }
-      }
-      acc[i].add(sg);
-      acc[G + i].add(yg);
-      if constexpr (NEWP) {
-        acc[2 * G + i].add(sn);
-        acc[3 * G + i].add(yn2);
       }
     }
   }

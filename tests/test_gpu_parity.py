@@ -284,3 +284,63 @@ def test_full_size_256_plane_wave_and_symmetry():
     assert (torch.linalg.vector_norm((GHu - Hu).double()) / torch.linalg.vector_norm(Hu.double())).item() < 1e-5
     assert torch.sum(u.double() * Hu.double()).item() > 0
     s.close()
+
+
+def test_laminate_closed_form_256cube_fp32():
+    """The 256^3 bilayer laminate of the full-size configuration, general
+    strain-controlled load with Poisson coupling, FP32 fields: per-layer
+    strains of the closed form (written out from the interface conditions)
+    within 1e-4 of the largest strain (the strain-field bound)."""
+    from tests.test_oracle_solver import _laminate_exact
+    dims = (256, 256, 256)
+    pm = laminate(dims, axis=2)
+    pa, pb = (1.0, 0.3, False, 0.0, 0.0), (10.0, 0.2, False, 0.0, 0.0)
+    E = np.array([2e-4, -1e-4, 1e-3, 3e-4, -2e-4, 1e-4])
+    s = _solver(dims, pm, [pa, pb], 32, eta_eq=1e-6, eta_cg=1e-4)
+    rep = s.solve_step(E)
+    assert rep["converged"]
+    ea, eb = _laminate_exact(oracle.Phase(1.0, 0.3), oracle.Phase(10.0, 0.2), E)
+    eps = s.get_state()["eps"]
+    scale = float(np.abs(np.concatenate([ea, eb])).max())
+    ta = torch.tensor(ea, dtype=torch.float32, device=eps.device).view(6, 1, 1, 1)
+    tb = torch.tensor(eb, dtype=torch.float32, device=eps.device).view(6, 1, 1, 1)
+    assert float((eps[:, :128] - ta).abs().max()) < 1e-4 * scale
+    assert float((eps[:, 128:] - tb).abs().max()) < 1e-4 * scale
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_load_path_mixed_shear_uniaxial(precision):
+    """Mixed load path: eps_zz and the shear eps_yz ramped together (the
+    other components stress-free) on a ragged 12x10x8 sphere cell, through
+    the elastic increment and three increments of growing damage before the
+    peak: homogenised eps_zz and shear stresses against the oracle (1e-5
+    elastic, 1e-4 damaged), same damaged voxels."""
+    from oracle.solver import TRParams
+    dims = (12, 10, 8)
+    pm = random_spheres(dims, count=3, rmin=1.5, rmax=2.5, seed=11)
+    phases = [MATRIX, STIFF]
+    free = [1, 1, 0, 0, 1, 1]
+    inc = np.array([0, 0, 2e-5, np.sqrt(2) * 1e-5, 0, 0])
+    incs = [inc] * 4
+    R0 = 10 * np.sqrt(pm.size) * np.linalg.norm(inc)
+    ref = _oracle_curve(pm, phases, incs, np.array(free, bool),
+                        TRParams(eta_eq=1e-8, eta_cg=1e-2, R0=R0, Rmax=R0, max_nr=400))
+    eta = 1e-8 if precision == 64 else 1e-6
+    s = _solver(dims, pm, phases, precision, eta_eq=eta, eta_cg=1e-2, R0=R0, Rmax=R0, max_nr=400)
+    out = []
+    for dE in incs:
+        rep = s.solve_step(dE, free_mask=free)
+        assert rep["converged"]
+        out.append(rep["mean_stress"])
+    out = np.array(out)
+    sref = ref["mean_stress"]
+    for n in range(4):
+        tol = 1e-5 if n == 0 else 1e-4
+        for c in (2, 3):
+            assert abs(out[n, c] - sref[n, c]) <= tol * abs(sref[n, c]), (n, c, out[n, c], sref[n, c])
+    kap = s.get_state()["kappa"].cpu().numpy().astype(np.float64)
+    near = np.abs(ref["kappa"] - 1e-4) <= 1e-3 * 1e-4
+    assert (ref["kappa"] > 1e-4).any()
+    assert np.array_equal((kap > 1e-4)[~near], (ref["kappa"] > 1e-4)[~near])
+    s.close()

@@ -139,25 +139,6 @@ __global__ void __launch_bounds__(kFT)
   constexpr int LITEMS = NL * NXH;
   constexpr int LSTEPS = (LITEMS + kFT - 1) / kFT;
   constexpr int LB = LSTEPS < 4 ? LSTEPS : 4;
-  if constexpr (CG) {
-    // The CG update reads z, d (and r) only after the inverse transform:
-    // start bringing this block's rows of them into L2 now, one bulk
-    // prefetch per component and field (contiguous rows row0 .. row0+Q-1),
-    // so that those reads overlap the shared-memory FFT instead of following
-    // it.  Rows are N floats long, so every segment starts and ends on a
-    // 16-byte boundary.
-    if (threadIdx.x < 3 * NC) {
-      const int f = threadIdx.x / NC, c = threadIdx.x - (threadIdx.x / NC) * NC;
-      const long long nq = min((long long)Q, nrows - row0);
-      const int status = *cstatus;
-      const float* base = f == 0 ? cz : (f == 1 ? cd : cr);
-      if (nq > 0 && (f < 2 ? (status == 0 || status == 2 || status == 3) : status == 0)) {
-        const float* seg = base + c * nvox + row0 * N;
-        const unsigned bytes = (unsigned)(nq * N * sizeof(float));
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(seg), "r"(bytes) : "memory");
-      }
-    }
-  }
   for (int s0 = 0; s0 < LSTEPS; s0 += LB) {
     float2 xh[LB][2];
 #pragma unroll

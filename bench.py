@@ -87,10 +87,12 @@ def _args():
     p.add_argument("--n", type=int, default=N, help="grid size (default 256)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default="rve256",
-                   choices=["rve256", "asr", "lbfgs", "batch96", "warmstart", "hv"],
+                   choices=["rve256", "asr", "lbfgs", "onset", "batch96", "warmstart", "hv"],
                    help="rve256: the 256^3 sphere cell (default); asr: the same cell as an ASR-like "
                         "aggregate / paste / gel model loaded by gel eigenstrain; lbfgs: the default load step "
-                        "solved by L-BFGS and by trust-region Newton-CG; batch96: 96 cells of uneven sizes; "
+                        "solved by L-BFGS and by trust-region Newton-CG; onset: a load step at the onset of "
+                        "damage with the secant and the symmetric consistent Hessian; batch96: 96 cells of "
+                        "uneven sizes; "
                         "warmstart: train the spectral neural operator, then learned vs plain load steps; "
                         "hv: Hessian-vector products alone (damage snapshot, compatible input), several sizes")
     p.add_argument("--lbfgs-memory", type=int, default=5, help="lbfgs: (s, y) pairs kept")
@@ -128,7 +130,7 @@ def _kernel_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2207_10657_gb300", "csrc")
     skip = {"fno.cu", "batch.cu", "noalloc.cu", "lbfgs.cu", "lbfgs.cuh", "homogenize.cu", "homogenize.cuh",
-            "rve_api.cu"}
+            "consistent.cu", "consistent.cuh", "rve_api.cu"}
     for fn in sorted(os.listdir(csrc)):
         if fn.endswith((".cu", ".cuh")) and fn not in skip:
             with open(os.path.join(csrc, fn), "rb") as f:
@@ -652,6 +654,70 @@ def run_lbfgs(args):
     return 0
 
 
+ONSET_WORKLOAD = ("128^3 random-sphere cell (48 spheres, r~U[4,10], seed 0; the materials of the load-step "
+                  "workload), uniaxial eps_zz (other components stress-free): after a first increment of 5e-5 "
+                  "(damage starts), a step = the next increment of 2e-5 from that state (reset every step), "
+                  "trust-region Newton + Steihaug CG to rel. residual 1e-6, with the secant Hessian and with the "
+                  "symmetric consistent tangent")
+
+
+def run_onset(args):
+    """One load step at the damage onset with the secant and with the
+    symmetric consistent Hessian (the converged state of a first increment
+    is the reference state of every timed step)."""
+    import torch
+    from paper_2207_10657_gb300 import RVESolver, build as _build
+    from synth import random_spheres
+    _build.build()
+    n = 128
+    dims = (n, n, n)
+    pm = random_spheres(dims, count=48, rmin=4.0, rmax=10.0, seed=0)
+    st = torch.cuda.Stream()
+    R0 = 10.0 * (n ** 3) ** 0.5 * 5e-5
+    dE1, dE2 = [0.0, 0.0, 5e-5, 0.0, 0.0, 0.0], [0.0, 0.0, 2e-5, 0.0, 0.0, 0.0]
+    out = {}
+    for name, h in (("secant", 0), ("consistent", 1)):
+        with torch.cuda.stream(st):
+            s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, stream=st, eta_eq=1e-6, eta_cg=1e-2,
+                          max_nr=2000, R0=R0, Rmax=R0, hessian=h)
+        first = s.solve_step(dE1, free_mask=FREE, raise_on_error=False)
+        ref = s.get_state()
+        eps0, kap0 = ref["eps"].clone(), ref["kappa"].clone()
+
+        def step():
+            s.set_state(eps0, kap0)
+            return s.solve_step(dE2, free_mask=FREE, raise_on_error=False)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        hv0, l0 = s.hv_count, s.launch_count
+        ev0.record(st)
+        reps = [step() for _ in range(args.steps)]
+        ev1.record(st)
+        torch.cuda.synchronize()
+        out[name] = {"ms": ev0.elapsed_time(ev1) / args.steps, "hv": (s.hv_count - hv0) / args.steps,
+                     "launches": s.launch_count - l0, "first_nr": first["nr_iters"],
+                     "nr_iters": [r["nr_iters"] for r in reps], "converged": [r["converged"] for r in reps],
+                     "mean_stress_zz": [r["mean_stress"][2] for r in reps],
+                     "damaged_voxels": int((s.get_state()["kappa"] > 1e-4).sum().item())}
+        s.close()
+    c, sc = out["consistent"], out["secant"]
+    line = {
+        "metric": "load-step time at the damage onset, 128³: symmetric consistent vs secant Hessian",
+        "value": c["ms"], "unit": "ms/load step", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": c["ms"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": ONSET_WORKLOAD, "consistent": c, "secant": sc,
+                   "speedup_over_secant": sc["ms"] / c["ms"],
+                   "voxel_hv_per_s_consistent": c["hv"] * n ** 3 / (c["ms"] / 1e3)},
+        "gpu_launches": c["launches"],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 WS_WORKLOAD = ("learned warm start: 4-layer spectral neural operator (width 32, modes kx<16, |ky|,|kz|<=8, BF16 "
                "operands, FP32 accumulation) trained on plain-solver load steps of seeded 64^3 sphere cells (48 "
                "spheres, r~U[2,5]) under uniaxial eps_zz increments of 1e-5 (other components stress-free), then "
@@ -831,6 +897,8 @@ def main():
         return run_hv(args)
     if args.workload == "lbfgs":
         return run_lbfgs(args)
+    if args.workload == "onset":
+        return run_onset(args)
     return run_gpu(args)
 
 

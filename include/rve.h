@@ -77,6 +77,15 @@ typedef struct {
   int max_nr, max_cg; /* Newton and CG iteration caps */
   double restart_thr; /* Powell restart threshold, Eq. (20): 0.2 */
   int precision;      /* 32 (FP32 fields) or 64 (FP64 fields) */
+  int hessian;        /* 0: secant (1-D) C (default); 1: symmetric part of the
+                         consistent damage tangent, (1-D) C - D'(kappa)/2
+                         ((C:eps) (x) n + n (x) (C:eps)) with n = eps^(t)/kappa
+                         on loading voxels (Appendix A; kappa^2 is a spectral
+                         function of eps, so d kappa/d eps = n).  Used by the
+                         Hessian-vector products and the model change of the
+                         trust-region step; costs 4 B/voxel per product plus
+                         C:eps and n on loading voxels, and 13 reals per voxel
+                         of storage.  The batched solver keeps the secant. */
 } rve_solver_opts;
 
 /* Per-load-step statistics. */
@@ -90,7 +99,7 @@ typedef struct {
 
 /* Fill opts with defaults: eta_eq 1e-6, eta_nr 0, eta_cg 1e-2, eta_up 0.1,
  * R0 = Rmax = 0 (meaning "10 sqrt(Nvox) |dE|" at the first load step),
- * max_nr 50, max_cg 1000, restart_thr 0.2, precision 32. */
+ * max_nr 50, max_cg 1000, restart_thr 0.2, precision 32, hessian 0. */
 void rve_default_opts(rve_solver_opts* opts);
 
 /* Create a context.  Sec. 2 (cell, strain split), Appendix A (phases).
@@ -143,11 +152,12 @@ rve_status rve_set_free_mask(rve_t, const uint8_t free_mask_host[6]);
  * eigenstrain.  RVE_ERR_ARG on a wrong nphase or a non-finite entry. */
 rve_status rve_set_eigenstrain(rve_t, const double* eig_host, int nphase);
 
-/* Hessian-vector product of Eq. (8) with the secant tangent frozen at the
- * state: out = G : ((1 - D) C : v).  v_dev, out_dev: ncomp x Nvox real; they
- * may alias.  The product is: tangent (Eq. (13)), forward real FFT,
- * per-frequency projection Ghat(k) from the FE gradient (Eqs. (5), (9)),
- * inverse FFT. */
+/* Hessian-vector product of Eq. (8) with the tangent frozen at the state:
+ * out = G : ((1 - D) C : v) (secant), or with the symmetric consistent
+ * tangent of the state when the context was created with opts.hessian = 1.
+ * v_dev, out_dev: ncomp x Nvox real; they may alias.  The product is:
+ * tangent (Eq. (13)), forward real FFT, per-frequency projection Ghat(k)
+ * from the FE gradient (Eqs. (5), (9)), inverse FFT. */
 rve_status rve_hessp(rve_t, const void* v_dev, void* out_dev);
 
 /* Projection alone, out = G : v (Eqs. (4)-(5)).  May alias. */

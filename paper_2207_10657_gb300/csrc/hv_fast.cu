@@ -31,11 +31,14 @@ template <int N> constexpr int zminblocks() { return N >= 512 ? 1 : 3; }
 template <int N> constexpr int p2tx() { return (kFBudget / (3 * N)) < 16 ? (kFBudget / (3 * N)) : 16; }
 
 // ------------------------------------------------------------ x forward
+// MODE 0: plain; 1: secant tangent; 2: symmetric consistent tangent (the
+// secant plus the rank-one correction of ConsTan on loading voxels).
 template <int N, int NC, int MODE>
 __global__ void __launch_bounds__(kFT)
     kf_xfwd(const float* __restrict__ in, const uint8_t* __restrict__ phase, const float* __restrict__ dmg,
             const MatTable<float> mt, float2* __restrict__ spec, const long long nrows, const long long nvox,
-            const float2* __restrict__ tw, double* __restrict__ partials) {
+            const float2* __restrict__ tw, double* __restrict__ partials, const float* __restrict__ cdp = nullptr,
+            const float* __restrict__ ca = nullptr, const float* __restrict__ cn = nullptr) {
   constexpr int Q = xq<N, NC>();
   constexpr int NL = NC * Q / 2;
   constexpr int ND = NC == 6 ? 3 : 2;
@@ -59,17 +62,31 @@ __global__ void __launch_bounds__(kFT)
       const long long vox = row * N + x;
 #pragma unroll
       for (int c = 0; c < NC; ++c) v[b][c] = ok ? __ldg(in + c * nvox + vox) : 0.f;
-      if (MODE == 1 && ok) {
+      if (MODE >= 1 && ok) {
         const float keep = 1.f - __ldg(dmg + vox);
         const int ph = __ldg(phase + vox);
         const float lam = mt.lam[ph] * keep, tmu = 2.f * mt.mu[ph] * keep;
         float tr = 0.f;
 #pragma unroll
         for (int i = 0; i < ND; ++i) tr += v[b][i];
+        float hdp = 0.f, nv = 0.f, av = 0.f;
+        if constexpr (MODE == 2) {
+          hdp = 0.5f * __ldg(cdp + vox);
+          if (hdp != 0.f) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+              nv += __ldg(cn + c * nvox + vox) * v[b][c];
+              av += __ldg(ca + c * nvox + vox) * v[b][c];
+            }
+          }
+        }
         float dv = 0.f;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          const float sg = tmu * v[b][c] + (c < ND ? lam * tr : 0.f);
+          float sg = tmu * v[b][c] + (c < ND ? lam * tr : 0.f);
+          if constexpr (MODE == 2) {
+            if (hdp != 0.f) sg -= hdp * (__ldg(ca + c * nvox + vox) * nv + __ldg(cn + c * nvox + vox) * av);
+          }
           dv += v[b][c] * sg;
           v[b][c] = sg;
         }
@@ -106,7 +123,7 @@ __global__ void __launch_bounds__(kFT)
       if (row < nrows) spec[(c * nrows + row) * NXH + k] = h ? xb : xa;
     }
   }
-  if (MODE == 1 && partials) {
+  if (MODE >= 1 && partials) {
     double val[1] = {(double)acc};
     block_sum<1>(val, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = val[0];
@@ -401,19 +418,26 @@ bool fast_size(int n) {
 template <int N>
 static cudaError_t xfwd_n(const GridDesc& g, const float* in, const uint8_t* phase, const float* dmg,
                           const MatTable<float>& mt, float2* spec, const float2* tw, bool tangent, double* partials,
-                          int* nblocks, cudaStream_t st) {
+                          int* nblocks, cudaStream_t st, const ConsTan<float>* ct) {
   double* pd = tangent ? partials : nullptr;
+  const bool cons = tangent && ct && ct->dp;
   if (g.ncomp == 6) {
     constexpr int Q = xq<N, 6>();
     const int blocks = (int)((g.nrows + Q - 1) / Q);
     *nblocks = blocks;
-    if (tangent) kf_xfwd<N, 6, 1><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw, pd);
+    if (cons)
+      kf_xfwd<N, 6, 2><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw, pd, ct->dp, ct->a,
+                                                ct->n);
+    else if (tangent) kf_xfwd<N, 6, 1><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw, pd);
     else kf_xfwd<N, 6, 0><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw, nullptr);
   } else {
     constexpr int Q = xq<N, 3>();
     const int blocks = (int)((g.nrows + Q - 1) / Q);
     *nblocks = blocks;
-    if (tangent) kf_xfwd<N, 3, 1><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw, pd);
+    if (cons)
+      kf_xfwd<N, 3, 2><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw, pd, ct->dp, ct->a,
+                                                ct->n);
+    else if (tangent) kf_xfwd<N, 3, 1><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw, pd);
     else kf_xfwd<N, 3, 0><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw, nullptr);
   }
   return cudaGetLastError();
@@ -474,9 +498,9 @@ static cudaError_t yproj2d_n(const GridDesc& g, float2* spec, const SpecWork<flo
 
 cudaError_t fast_xfwd(const GridDesc& g, const float* in, const uint8_t* phase, const float* dmg,
                       const MatTable<float>& mt, float2* spec, const float2* tw, bool tangent, double* partials,
-                      int* nblocks, cudaStream_t st) {
+                      int* nblocks, cudaStream_t st, const ConsTan<float>* ct) {
 #define RVE_CASE(n_) \
-  if (g.nx == n_) return xfwd_n<n_>(g, in, phase, dmg, mt, spec, tw, tangent, partials, nblocks, st);
+  if (g.nx == n_) return xfwd_n<n_>(g, in, phase, dmg, mt, spec, tw, tangent, partials, nblocks, st, ct);
   RVE_FAST_SIZES(RVE_CASE)
 #undef RVE_CASE
   return cudaErrorNotSupported;

@@ -10,9 +10,11 @@ namespace rve {
 bool fast_size(int n);
 // With `partials` (tangent mode only) every block also writes its sum of
 // in : (tangent : in) to partials[block]; *nblocks receives the block count.
+// ct (may be NULL): with ct->dp set, the tangent mode applies the symmetric
+// consistent tangent instead of the secant.
 cudaError_t fast_xfwd(const GridDesc& g, const float* in, const uint8_t* phase, const float* dmg,
                       const MatTable<float>& mt, float2* spec, const float2* tw, bool tangent, double* partials,
-                      int* nblocks, cudaStream_t st);
+                      int* nblocks, cudaStream_t st, const ConsTan<float>* ct = nullptr);
 cudaError_t fast_xinv(const GridDesc& g, const float2* spec, float* out, const float* dotw, double* partials,
                       const float2* tw, bool dot, bool self, int* nblocks, cudaStream_t st);
 // x-inverse that applies the Steihaug-CG iterate / residual update with the

@@ -248,15 +248,16 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
     if (fast_size(g.nx)) {
       const bool want = mode == XIn::Tangent && dot_with != nullptr && dot_with == in;
       e = fast_xfwd(g, in, phase, damage, mt, w.spec, w.tw[0], mode == XIn::Tangent, want ? w.partials : nullptr,
-                    &fwd_blocks, st);
+                    &fwd_blocks, st, &w.cons);
       fwd_dot = want && e == cudaSuccess;
     }
   }
   if (e == cudaErrorNotSupported) {
     if (mode == XIn::Tangent)
-      k_xfwd<R, 1><<<xblocks, kXThreads, xsm, st>>>(in, phase, damage, mt, w.spec, g, w.qx, w.px, w.tw[0]);
+      k_xfwd<R, 1><<<xblocks, kXThreads, xsm, st>>>(in, phase, damage, mt, w.spec, g, w.qx, w.px, w.tw[0], w.cons);
     else
-      k_xfwd<R, 0><<<xblocks, kXThreads, xsm, st>>>(in, phase, damage, mt, w.spec, g, w.qx, w.px, w.tw[0]);
+      k_xfwd<R, 0><<<xblocks, kXThreads, xsm, st>>>(in, phase, damage, mt, w.spec, g, w.qx, w.px, w.tw[0],
+                                                    ConsTan<R>{});
     e = cudaGetLastError();
   }
   }
@@ -305,7 +306,7 @@ cudaError_t spectral_hv_cg(const GridDesc& g, SpecWork<float>& w, const MatTable
   int fb = 0, ib = 0;
   {
     PassScope ps(w.timer, st, PASS_XFWD);
-    e = fast_xfwd(g, d, phase, damage, mt, w.spec, w.tw[0], true, w.partials, &fb, st);
+    e = fast_xfwd(g, d, phase, damage, mt, w.spec, w.tw[0], true, w.partials, &fb, st, &w.cons);
   }
   if (e != cudaSuccess) return e;
   ++nl;

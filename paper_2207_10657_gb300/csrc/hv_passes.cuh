@@ -15,6 +15,16 @@ struct GridDesc {
   long long nrows;  // ny * nz voxel rows along x
 };
 
+// Rank-one part of the symmetric consistent damage tangent, per voxel: the
+// tangent applied to v is (1-D) C : v - dp/2 (a (n.v) + n (a.v)) with
+// a = C : eps, n = eps^(t) / kappa and dp = D'(kappa) on loading voxels
+// (0 elsewhere; a and n are read only where dp != 0).  All NULL: secant.
+template <typename R> struct ConsTan {
+  const R* dp = nullptr;  // Nvox
+  const R* a = nullptr;   // ncomp x Nvox
+  const R* n = nullptr;   // ncomp x Nvox
+};
+
 // Tables and workspace for the spectral passes at precision R.
 template <typename R> struct SpecWork {
   AxisPlan px, py, pz;
@@ -30,6 +40,7 @@ template <typename R> struct SpecWork {
   double* partials = nullptr;  // per-block FP64 partial sums (epilogues)
   int max_partials = 0;
   PassTimer* timer = nullptr;  // optional per-pass event timing
+  ConsTan<R> cons;             // set: tangent passes apply the consistent tangent
 };
 
 enum class XIn { Plain = 0, Tangent = 1 };

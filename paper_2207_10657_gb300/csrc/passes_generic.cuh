@@ -16,14 +16,16 @@ constexpr int kSmemCap = 100 * 1024;        // dynamic shared memory cap per blo
 // ------------------------------------------------------------ x forward
 // Q voxel rows per block, all ncomp components of each row.  With the
 // tangent mode the damaged isotropic tangent (1-D)(lambda tr(v) 1 + 2 mu v)
-// is applied on load (Eq. (13), secant reading).  Real rows are packed in
-// pairs into one complex FFT (real + i*imag) and separated with the
+// is applied on load (Eq. (13), secant reading), plus the rank-one part of
+// the symmetric consistent tangent where `ct` is set.  Real rows are packed
+// in pairs into one complex FFT (real + i*imag) and separated with the
 // Hermitian symmetry of real-input spectra.
 template <typename R, int MODE>
 __device__ __forceinline__ void xfwd_body(const R* __restrict__ in, const uint8_t* __restrict__ phase,
                                           const R* __restrict__ dmg, const MatTable<R>& mt,
                                           Cx<R>* __restrict__ spec, const GridDesc& g, const int Q,
-                                          const AxisPlan& px, const Cx<R>* __restrict__ tw, const int bx) {
+                                          const AxisPlan& px, const Cx<R>* __restrict__ tw, const int bx,
+                                          const ConsTan<R> ct = ConsTan<R>{}) {
   using C = Cx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -43,7 +45,18 @@ __device__ __forceinline__ void xfwd_body(const R* __restrict__ in, const uint8_
         const R lam = mt.lam[ph] * keep, two_mu = (R)2 * mt.mu[ph] * keep;
         R tr = 0;
         for (int i = 0; i < nd; ++i) tr += val[i];
-        for (int c = 0; c < nc; ++c) val[c] = two_mu * val[c] + (c < nd ? lam * tr : (R)0);
+        const R hdp = ct.dp ? (R)0.5 * ct.dp[vox] : (R)0;
+        R nv = 0, av = 0;
+        if (hdp != (R)0) {
+          for (int c = 0; c < nc; ++c) {
+            nv += ct.n[c * g.nvox + vox] * val[c];
+            av += ct.a[c * g.nvox + vox] * val[c];
+          }
+        }
+        for (int c = 0; c < nc; ++c) {
+          val[c] = two_mu * val[c] + (c < nd ? lam * tr : (R)0);
+          if (hdp != (R)0) val[c] -= hdp * (ct.a[c * g.nvox + vox] * nv + ct.n[c * g.nvox + vox] * av);
+        }
       }
     }
     for (int c = 0; c < nc; ++c) {
@@ -75,8 +88,8 @@ template <typename R, int MODE>
 __global__ void __launch_bounds__(kXThreads)
     k_xfwd(const R* __restrict__ in, const uint8_t* __restrict__ phase, const R* __restrict__ dmg,
            const MatTable<R> mt, Cx<R>* __restrict__ spec, const GridDesc g, const int Q, const AxisPlan px,
-           const Cx<R>* __restrict__ tw) {
-  xfwd_body<R, MODE>(in, phase, dmg, mt, spec, g, Q, px, tw, blockIdx.x);
+           const Cx<R>* __restrict__ tw, const ConsTan<R> ct) {
+  xfwd_body<R, MODE>(in, phase, dmg, mt, spec, g, Q, px, tw, blockIdx.x, ct);
 }
 
 // ------------------------------------------------------------ y columns

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/rve.h"
+#include "consistent.cuh"
 #include "homogenize.cuh"
 #include "hv_passes.cuh"
 #include "lbfgs.cuh"
@@ -49,6 +50,8 @@ struct Impl {
   R *eps = nullptr, *sig = nullptr, *sig_t = nullptr, *g = nullptr, *z = nullptr, *r = nullptr, *d = nullptr,
     *Hd = nullptr, *tmp = nullptr;
   R *D = nullptr, *D_t = nullptr, *kap = nullptr, *kap_t = nullptr, *khist = nullptr;
+  // symmetric consistent tangent of the state (opts.hessian = 1 only)
+  R *cdp = nullptr, *ca = nullptr, *cn = nullptr;
   DevScalars* S = nullptr;
   // L-BFGS pairs (allocated at the first L-BFGS step; lb_mem of each)
   int lb_mem = 0;
@@ -112,7 +115,7 @@ void impl_free(Impl<R>* m) {
   if (!m) return;
   spectral_free(m->sw);
   void* ptrs[] = {m->phase, m->eps, m->sig, m->sig_t, m->g, m->z, m->r, m->d, m->Hd, m->tmp,
-                  m->D, m->D_t, m->kap, m->kap_t, m->khist, m->S};
+                  m->D, m->D_t, m->kap, m->kap_t, m->khist, m->cdp, m->ca, m->cn, m->S};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < kLbMaxMemory; ++i) {
@@ -130,6 +133,15 @@ rve_status read_scalars(rve_ctx* c) {
   CK(cudaMemcpyAsync(c->Sh, m->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->st), "read scalars");
   CK(cudaStreamSynchronize(c->st), "synchronize");
   return RVE_OK;
+}
+
+// With the consistent Hessian, refresh its per-voxel data from the state
+// (strain eps, committed history); a no-op with the secant.
+template <typename R>
+cudaError_t refresh_hessian(rve_ctx* c) {
+  Impl<R>* m = impl_of<R>(c);
+  if (!m->cdp) return cudaSuccess;
+  return cons_prep<R>(c->g, m->mt, m->eg, m->phase, m->eps, m->khist, m->cdp, m->ca, m->cn, c->st, &c->launches);
 }
 
 template <typename R>
@@ -160,6 +172,12 @@ rve_status create_impl(rve_ctx* c, const uint8_t* phase_ids, const rve_phase* ph
   for (R** f : fields) CK(cudaMalloc(f, nf), "field allocation");
   R** sf[] = {&m->D, &m->D_t, &m->kap, &m->kap_t, &m->khist};
   for (R** f : sf) CK(cudaMalloc(f, ns), "scalar-field allocation");
+  if (c->opts.hessian == 1) {
+    CK(cudaMalloc(&m->cdp, ns), "consistent-tangent allocation");
+    CK(cudaMalloc(&m->ca, nf), "consistent-tangent allocation");
+    CK(cudaMalloc(&m->cn, nf), "consistent-tangent allocation");
+    m->sw.cons = ConsTan<R>{m->cdp, m->ca, m->cn};
+  }
   CK(cudaMalloc(&m->phase, g.nvox), "phase allocation");
   CK(cudaMalloc(&m->S, sizeof(DevScalars)), "scalar allocation");
   CK(cudaMemsetAsync(m->S, 0, sizeof(DevScalars), c->st), "memset");
@@ -177,6 +195,7 @@ rve_status create_impl(rve_ctx* c, const uint8_t* phase_ids, const rve_phase* ph
   CK(trial_eval<R>(g, m->mt, m->eg, m->phase, m->eps, nullptr, m->khist, nullptr, nullptr, m->sig, m->D, m->kap, m->S,
                    m->sw.partials, c->st, &c->launches),
      "initial state");
+  CK(refresh_hessian<R>(c), "consistent tangent");
   CK(cudaStreamSynchronize(c->st), "synchronize");
   return RVE_OK;
 }
@@ -290,6 +309,7 @@ rve_status solve_step_impl(rve_ctx* c, const double dE[6], const void* init, rve
   CK(trial_eval<R>(g, m->mt, m->eg, m->phase, m->eps, nullptr, m->khist, nullptr, nullptr, m->sig, m->D, m->kap, m->S,
                    m->sw.partials, c->st, nl),
      "stress");
+  CK(refresh_hessian<R>(c), "consistent tangent");
   rve_status s = gradient<R>(c);
   if (s != RVE_OK) return s;
   if ((s = read_scalars<R>(c)) != RVE_OK) return s;
@@ -301,7 +321,7 @@ rve_status solve_step_impl(rve_ctx* c, const double dE[6], const void* init, rve
     {
       PassScope ps(&c->timer, c->st, PASS_TRIAL);
       CK(trial_eval<R>(g, m->mt, m->eg, m->phase, m->eps, m->z, m->khist, m->sig, m->D, m->sig_t, m->D_t, m->kap_t,
-                       m->S, m->sw.partials, c->st, nl),
+                       m->S, m->sw.partials, c->st, nl, m->sw.cons),
          "trial stress");
     }
     CK(tr_decide(m->S, c->st, nl), "ratio test");
@@ -319,6 +339,7 @@ rve_status solve_step_impl(rve_ctx* c, const double dE[6], const void* init, rve
     std::swap(m->sig, m->sig_t);
     std::swap(m->D, m->D_t);
     std::swap(m->kap, m->kap_t);
+    CK(refresh_hessian<R>(c), "consistent tangent");
     if ((s = gradient<R>(c)) != RVE_OK) return s;
     if ((s = read_scalars<R>(c)) != RVE_OK) return s;
     rel = sts > 0 ? std::sqrt(c->Sh->gg / sts) : 0.0;
@@ -497,6 +518,7 @@ rve_status lbfgs_step_impl(rve_ctx* c, const double dE[6], int mem, int max_iter
     }
     rel = sts > 0 ? std::sqrt(c->Sh->gg / sts) : 0.0;
   }
+  CK(refresh_hessian<R>(c), "consistent tangent");
   CK(field_means<R>(g, m->sig, m->eps, m->S, part, c->st, nl), "means");
   if ((s = read_scalars<R>(c)) != RVE_OK) return s;
   for (int i = 0; i < 6; ++i) {
@@ -531,6 +553,8 @@ rve_status stiffness_impl(rve_ctx* c, double tol, int max_cg, double* Cbar, int*
   const double R0 = c->R, Rm = c->Rmax;
   const rve_solver_opts opts0 = c->opts;
   const unsigned fm0 = m->sw.free_mask;
+  const ConsTan<R> ct0 = m->sw.cons;
+  m->sw.cons = ConsTan<R>{};  // the effective stiffness is the secant one
   c->R = c->Rmax = 1e300;
   c->opts.eta_cg = tol;
   c->opts.max_cg = max_cg;
@@ -540,6 +564,7 @@ rve_status stiffness_impl(rve_ctx* c, double tol, int max_cg, double* Cbar, int*
     c->Rmax = Rm;
     c->opts = opts0;
     m->sw.free_mask = fm0;
+    m->sw.cons = ct0;
   };
   rve_status s = RVE_OK;
   rve_step_report rep{};
@@ -591,6 +616,7 @@ rve_status set_state_impl(rve_ctx* c, const void* strain, const void* khist) {
   CK(trial_eval<R>(g, m->mt, m->eg, m->phase, m->eps, nullptr, m->khist, nullptr, nullptr, m->sig, m->D, m->kap, m->S,
                    m->sw.partials, c->st, &c->launches),
      "state stress");
+  CK(refresh_hessian<R>(c), "consistent tangent");
   return RVE_OK;
 }
 
@@ -609,6 +635,7 @@ rve_status set_eig_impl(rve_ctx* c, const double* eig) {
   CK(trial_eval<R>(g, m->mt, m->eg, m->phase, m->eps, nullptr, m->khist, nullptr, nullptr, m->sig, m->D, m->kap,
                    m->S, m->sw.partials, c->st, &c->launches),
      "state stress");
+  CK(refresh_hessian<R>(c), "consistent tangent");
   return RVE_OK;
 }
 
@@ -629,7 +656,7 @@ rve_status energy_grad_impl(rve_ctx* c, const void* p, double* dW, double* dm, v
   Impl<R>* m = impl_of<R>(c);
   const GridDesc& g = c->g;
   CK(trial_eval<R>(g, m->mt, m->eg, m->phase, m->eps, (const R*)p, m->khist, m->sig, m->D, m->sig_t, m->D_t, m->kap_t,
-                   m->S, m->sw.partials, c->st, &c->launches),
+                   m->S, m->sw.partials, c->st, &c->launches, m->sw.cons),
      "trial stress");
   k_energy_s<<<1, 1, 0, c->st>>>(m->S);
   ++c->launches;
@@ -671,6 +698,7 @@ void rve_default_opts(rve_solver_opts* o) {
   o->max_cg = 1000;
   o->restart_thr = 0.2;
   o->precision = 32;
+  o->hessian = 0;
 }
 
 rve_status rve_create(const int dims[3], int ndim, const uint8_t* phase_ids_dev, const rve_phase* phases, int nphase,
@@ -700,6 +728,10 @@ rve_status rve_create(const int dims[3], int ndim, const uint8_t* phase_ids_dev,
   if (c->opts.max_nr < 1 || c->opts.max_cg < 1) {
     delete c;
     return fail(nullptr, RVE_ERR_ARG, "max_nr and max_cg must be >= 1");
+  }
+  if (c->opts.hessian != 0 && c->opts.hessian != 1) {
+    delete c;
+    return fail(nullptr, RVE_ERR_ARG, "hessian must be 0 (secant) or 1 (symmetric consistent)");
   }
   c->precision = c->opts.precision;
   c->st = static_cast<cudaStream_t>(stream);

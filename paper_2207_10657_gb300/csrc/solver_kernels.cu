@@ -188,11 +188,13 @@ __global__ void __launch_bounds__(kVThreads)
 // ------------------------------------------------------- constitutive
 // With e = eps + p + eps_eig(phase): sigma_t = (1 - D_t) C : e,
 // kappa_t = max(kappa_n, kappa(e)) on damaging phases.  Sums (group T):
-// sig0:p, sig_t:p, p:(1-D0)C:p, sig_t:sig_t, p:p, (eps+p):(eps+p).
+// sig0:p, sig_t:p, p:B0:p, sig_t:sig_t, p:p, (eps+p):(eps+p), with B0 the
+// Hessian of the state: the secant (1-D0) C, plus the rank-one part of the
+// symmetric consistent tangent where `ct` is set.
 template <typename R, int NC>
 __global__ void __launch_bounds__(kVThreads)
-    k_trial(const GridDesc g, const MatTable<R> mt, const EigTable<R> eg, const uint8_t* __restrict__ phase,
-            const R* __restrict__ eps,
+    k_trial(const GridDesc g, const MatTable<R> mt, const EigTable<R> eg, const ConsTan<R> ct,
+            const uint8_t* __restrict__ phase, const R* __restrict__ eps,
             const R* __restrict__ p, const R* __restrict__ khist, const R* __restrict__ sig0,
             const R* __restrict__ D0, R* __restrict__ sig_t, R* __restrict__ D_t, R* __restrict__ kap_t,
             double* __restrict__ part) {
@@ -238,11 +240,22 @@ __global__ void __launch_bounds__(kVThreads)
 #pragma unroll
       for (int i = 0; i < nd; ++i) { tr += ev[i]; trp += pq[i]; }
       const R keep0 = (R)1 - elc<R>(d04, q);
+      const long long vq = 4 * v4 + q;
+      const R hdp = (ct.dp && p) ? (R)0.5 * ct.dp[vq] : (R)0;
+      R np_ = 0, ap_ = 0;
+      if (hdp != (R)0) {
+#pragma unroll
+        for (int c = 0; c < nc; ++c) {
+          np_ += ct.n[c * nv + vq] * pq[c];
+          ap_ += ct.a[c * nv + vq] * pq[c];
+        }
+      }
 #pragma unroll
       for (int c = 0; c < nc; ++c) {
         const R sv = keep * ((R)2 * mu * ev[c] + (c < nd ? lam * tr : (R)0));
         el<R>(sg[c], q) = sv;
-        const R bp = keep0 * ((R)2 * mu * pq[c] + (c < nd ? lam * trp : (R)0));
+        R bp = keep0 * ((R)2 * mu * pq[c] + (c < nd ? lam * trp : (R)0));
+        if (hdp != (R)0) bp -= hdp * (ct.a[c * nv + vq] * np_ + ct.n[c * nv + vq] * ap_);
         if (sig0) acc[0].add(elc<R>(s0[c], q) * pq[c]);
         acc[1].add(sv * pq[c]);
         acc[2].add(pq[c] * bp);
@@ -364,12 +377,12 @@ cudaError_t cg_dupdate(const GridDesc& g, const R* z, const R* r, R* d, DevScala
 template <typename R>
 cudaError_t trial_eval(const GridDesc& g, const MatTable<R>& mt, const EigTable<R>& eg, const uint8_t* phase,
                        const R* eps, const R* p, const R* khist, const R* sig0, const R* D0, R* sig_t, R* D_t,
-                       R* kap_t, DevScalars* S, double* part, cudaStream_t st, long long* nl) {
+                       R* kap_t, DevScalars* S, double* part, cudaStream_t st, long long* nl, const ConsTan<R>& ct) {
   if (g.ncomp == 6)
-    k_trial<R, 6><<<kVBlocks, kVThreads, 0, st>>>(g, mt, eg, phase, eps, p, khist, sig0, D0, sig_t, D_t, kap_t,
+    k_trial<R, 6><<<kVBlocks, kVThreads, 0, st>>>(g, mt, eg, ct, phase, eps, p, khist, sig0, D0, sig_t, D_t, kap_t,
                                                   part);
   else
-    k_trial<R, 3><<<kVBlocks, kVThreads, 0, st>>>(g, mt, eg, phase, eps, p, khist, sig0, D0, sig_t, D_t, kap_t,
+    k_trial<R, 3><<<kVBlocks, kVThreads, 0, st>>>(g, mt, eg, ct, phase, eps, p, khist, sig0, D0, sig_t, D_t, kap_t,
                                                   part);
   RVE_TRY(cudaGetLastError());
   *nl += 1;
@@ -419,7 +432,7 @@ cudaError_t field_means(const GridDesc& g, const R* sig, const R* eps, DevScalar
   template cudaError_t trial_eval<R>(const GridDesc&, const MatTable<R>&, const EigTable<R>&, const uint8_t*, \
                                      const R*, const R*,                                                        \
                                      const R*, const R*, const R*, R*, R*, R*, DevScalars*,                     \
-                                     double*, cudaStream_t, long long*);                                        \
+                                     double*, cudaStream_t, long long*, const ConsTan<R>&);                     \
   template cudaError_t axpy<R>(long long, R, const R*, R*, cudaStream_t, long long*);                          \
   template cudaError_t add_uniform<R>(const GridDesc&, R*, const double*, cudaStream_t, long long*);           \
   template cudaError_t field_means<R>(const GridDesc&, const R*, const R*, DevScalars*, double*, cudaStream_t, \

@@ -81,12 +81,14 @@ cudaError_t cg_dupdate(const GridDesc& g, const R* z, const R* r, R* d, DevScala
 // Trial constitutive evaluation at eps + p (p may be NULL), the material seeing
 // eps + p + eps_eig(phase): sigma_t, D_t, kappa_t, and group T sums against the
 // stored state (sig0, D0, may be NULL); the strain norm (eps+p):(eps+p) of the
-// group excludes the eigenstrain.
+// group excludes the eigenstrain.  p:B0:p uses the state's Hessian: the secant,
+// or the symmetric consistent tangent when ct is set.
 template <typename R>
 cudaError_t trial_eval(const GridDesc& g, const MatTable<R>& mt, const EigTable<R>& eg, const uint8_t* phase,
                        const R* eps, const R* p,
                        const R* khist, const R* sig0, const R* D0, R* sig_t, R* D_t, R* kap_t,
-                       DevScalars* S, double* part, cudaStream_t st, long long* nl);
+                       DevScalars* S, double* part, cudaStream_t st, long long* nl,
+                       const ConsTan<R>& ct = ConsTan<R>{});
 // rho_bar, radius update and acceptance (1 thread).
 cudaError_t tr_decide(DevScalars* S, cudaStream_t st, long long* nl);
 // y += a * x over ncomp * nvox entries (a from the host).

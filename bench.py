@@ -655,7 +655,7 @@ def run_lbfgs(args):
 
 
 ONSET_WORKLOAD = ("128^3 random-sphere cell (48 spheres, r~U[4,10], seed 0; the materials of the load-step "
-                  "workload), uniaxial eps_zz (other components stress-free): after a first increment of 4e-5 "
+                  "workload), uniaxial eps_zz (other components stress-free): after a first increment of 5e-5 "
                   "(damage starts), a step = the next increment of 5e-6 from that state (reset every step), "
                   "trust-region Newton + Steihaug CG to rel. residual 1e-6, with the secant Hessian and with the "
                   "symmetric consistent tangent")
@@ -673,8 +673,8 @@ def run_onset(args):
     dims = (n, n, n)
     pm = random_spheres(dims, count=48, rmin=4.0, rmax=10.0, seed=0)
     st = torch.cuda.Stream()
-    R0 = 10.0 * (n ** 3) ** 0.5 * 4e-5
-    dE1, dE2 = [0.0, 0.0, 4e-5, 0.0, 0.0, 0.0], [0.0, 0.0, 5e-6, 0.0, 0.0, 0.0]
+    R0 = 10.0 * (n ** 3) ** 0.5 * 5e-5
+    dE1, dE2 = [0.0, 0.0, 5e-5, 0.0, 0.0, 0.0], [0.0, 0.0, 5e-6, 0.0, 0.0, 0.0]
     out = {}
     for name, h in (("secant", 0), ("consistent", 1)):
         with torch.cuda.stream(st):

@@ -67,3 +67,32 @@ def test_default_opts_and_argument_errors(libpath):
     assert lib.rve_create(dims, 3, ctypes.c_void_p(16), bad, 1, None, None, ctypes.byref(h)) == -1
     assert lib.rve_create(dims, 4, ctypes.c_void_p(16), ph, 1, None, None, ctypes.byref(h)) == -1
     lib.rve_destroy(None)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of rve_phase, rve_solver_opts and rve_step_report
+    have the C sizes and field offsets (a host C program compiled against
+    include/rve.h prints them)."""
+    import shutil
+    import subprocess
+    from paper_2207_10657_gb300 import binding as B
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = {"rve_phase": B.rve_phase, "rve_solver_opts": B.rve_solver_opts, "rve_step_report": B.rve_step_report}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rve.h"', "int main(void) {"]
+    for s, cls in fields.items():
+        lines.append(f'  printf("{s} %zu\\n", sizeof({s}));')
+        for name, _ in cls._fields_:
+            lines.append(f'  printf("{s}.{name} %zu\\n", offsetof({s}, {name}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.split("\n") if l)
+    for s, cls in fields.items():
+        assert int(out[s]) == ctypes.sizeof(cls), s
+        for name, _ in cls._fields_:
+            assert int(out[f"{s}.{name}"]) == getattr(cls, name).offset, (s, name)

@@ -130,7 +130,8 @@ rve_status rve_get_state(rve_t, void* strain_dev, void* kappa_dev, void* stress_
 
 /* Replace the frozen damage field used by rve_hessp (Nvox values in [0,1],
  * context's real type).  For the Hessian-vector product on a damage
- * snapshot (benchmarks, tests). */
+ * snapshot (benchmarks, tests).  With opts.hessian = 1 the rank-one part of
+ * the consistent tangent stays the one of the last evaluated state. */
 rve_status rve_set_damage(rve_t, const void* damage_dev);
 
 /* Stress-controlled mean components (zero mean stress): free_mask[c] != 0

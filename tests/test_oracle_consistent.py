@@ -103,3 +103,54 @@ def test_consistent_hessian_reaches_the_secant_equilibrium_with_fewer_iterations
     n_sec = sum(r.nr_iters for r in sec["reports"])
     n_con = sum(r.nr_iters for r in con["reports"])
     assert n_con * 5 < n_sec, (n_con, n_sec)
+
+
+def test_full_tangent_newton_gmres_reaches_the_same_equilibrium():
+    """The full (non-symmetric) consistent tangent needs a non-symmetric inner
+    solver: inexact Newton with restarted GMRES on compatible directions and
+    a backtracking line search on the first-order energy of Eq. (18) reaches
+    the trust-region solvers' equilibrium at the damage onset in a handful
+    of Newton iterations."""
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    LinearOperator, gmres = sla.LinearOperator, sla.gmres
+    dims = (16, 12, 10)
+    pm = random_spheres(dims, count=3, rmin=2.0, rmax=3.0, seed=7)
+    phases = [oracle.Phase(1.0, 0.3, True, K0, KF), oracle.Phase(10.0, 0.2)]
+    free = np.array([True, True, False, True, True, True])
+    incs = [np.array([0, 0, 5e-5, 0, 0, 0]), np.array([0, 0, 2e-5, 0, 0, 0])]
+    rve = oracle.RVE(pm, phases, free_mask=free)
+    shape = (6,) + pm.shape
+    n = int(np.prod(shape))
+    eps, hist = np.zeros(shape), np.zeros(pm.shape)
+    newton = []
+    for dE in incs:
+        eps = eps + dE.reshape(6, 1, 1, 1)
+        sig, _, kap = rve.stress(eps, hist)
+        g = rve.G(sig)
+        its = 0
+        while rve.norm(g) > 1e-9 * rve.norm(sig) and its < 50:
+            its += 1
+
+            def mv(x, eps=eps):
+                v = rve.G(x.reshape(shape))
+                return rve.G(consistent_tangent_apply(v, eps, hist, rve.params)).reshape(-1) + (x - v.reshape(-1))
+
+            p, _ = gmres(LinearOperator((n, n), matvec=mv), -g.reshape(-1), rtol=1e-3, restart=50, maxiter=20)
+            p = rve.G(p.reshape(shape))
+            a, s0 = 1.0, rve.dot(sig, p)
+            for _ in range(30):
+                st, _, _ = rve.stress(eps + a * p, hist)
+                if 0.5 * (s0 + rve.dot(st, p)) * a <= 1e-4 * a * s0:
+                    break
+                a *= 0.5
+            eps = eps + a * p
+            sig, _, kap = rve.stress(eps, hist)
+            g = rve.G(sig)
+        newton.append(its)
+        hist = np.maximum(hist, kap)
+    R0 = 10 * np.sqrt(pm.size) * 5e-5
+    ref = load_path(oracle.RVE(pm, phases, free_mask=free), incs,
+                    TRParams(eta_eq=1e-9, eta_cg=1e-3, R0=R0, Rmax=R0, max_nr=500))
+    np.testing.assert_allclose(rve.mean(sig), ref["mean_stress"][-1], rtol=1e-7, atol=1e-14)
+    assert np.linalg.norm(eps - ref["eps"]) <= 1e-6 * np.linalg.norm(ref["eps"])
+    assert sum(newton) < 20, newton

@@ -111,3 +111,47 @@ def test_real_input_gives_real_projection_3d():
     z = random_field(6, (5, 4, 3), seed=7)
     gz, gzi = oracle.project(z, return_imag=True)
     assert np.max(np.abs(gzi)) < 1e-13
+
+
+def _per_frequency_projector(dhat):
+    """Dense orthogonal (Hermitian) projector onto {sym(Dhat (x) a), a in C^d}
+    in Mandel coordinates, from a pseudo-inverse (reading R2 written as its
+    definition, not as the closed form)."""
+    d = len(dhat)
+    cols = []
+    for j in range(d):
+        e = np.zeros(d, dtype=np.complex128)
+        e[j] = 1.0
+        t = 0.5 * (np.outer(dhat, e) + np.outer(e, dhat))
+        cols.append(oracle.tensor_to_mandel(t[None])[:, 0])
+    A = np.stack(cols, axis=1)
+    return A @ np.linalg.pinv(A, rcond=1e-12)
+
+
+@pytest.mark.parametrize("dims", [(4, 6), (5, 4), (4, 3, 6), (2, 4, 4)])
+def test_single_frequency_symbol_and_projector(dims):
+    """gradient_symbol_at / project_one (the per-frequency forms the 256^3
+    plane-wave GPU test uses) agree at every k of a small grid with the
+    full-grid symbol and with a dense per-frequency projector; project_one
+    also equals project_hat at that k (project_hat is pinned against the
+    dense real-space projector above)."""
+    d = len(dims)
+    ncomp = 3 if d == 2 else 6
+    shape = tuple(reversed(dims))
+    dh = oracle.gradient_symbol(shape)
+    zhat = RNG.standard_normal((ncomp,) + shape) + 1j * RNG.standard_normal((ncomp,) + shape)
+    ph = oracle.project_hat(zhat, dh, np.zeros(ncomp, bool))
+    for idx in np.ndindex(*shape):
+        k = tuple(reversed(idx))  # (kx, ky[, kz])
+        dk = oracle.gradient_symbol_at(k, dims)
+        np.testing.assert_allclose(dk, dh[(slice(None),) + idx], atol=1e-15)
+        z = zhat[(slice(None),) + idx]
+        got = oracle.project_one(z, dk)
+        if all(kk == 0 for kk in k):
+            continue  # k = 0 is the mean block, handled by project_hat alone
+        np.testing.assert_allclose(got, _per_frequency_projector(dk) @ z, atol=1e-12)
+        np.testing.assert_allclose(got, ph[(slice(None),) + idx], atol=1e-12)
+    # negative / aliased frequencies: the symbol is periodic in k
+    k = (1, -1) if d == 2 else (1, -1, 2)
+    kp = tuple(kk % n for kk, n in zip(k, dims))
+    np.testing.assert_allclose(oracle.gradient_symbol_at(k, dims), oracle.gradient_symbol_at(kp, dims), atol=0)

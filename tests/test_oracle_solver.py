@@ -217,3 +217,116 @@ def test_spring_modified_vs_standard_trust_region(alpha):
         assert len(r0.iterates) == len(r1.iterates)
         for a, b in zip(r0.iterates, r1.iterates):
             np.testing.assert_allclose(a, b, atol=1e-14)
+
+
+class _QuarticProblem:
+    """Dense non-quadratic test problem for Algorithm 2's radius and
+    acceptance rules: W(x) = 1/2 x.K x + g4 sum x^4 - c.x, gradient
+    sigma = K x + 4 g4 x^3 - c, Hessian B = K + 12 g4 diag(x^2).  No
+    projection (G = identity), no history."""
+
+    def __init__(self, K, g4, c):
+        self.K, self.g4, self.c = K, g4, c
+        self.stress_calls = []
+
+    def stress(self, x, hist):
+        self.stress_calls.append(np.array(x, copy=True))
+        return self.K @ x + 4.0 * self.g4 * x ** 3 - self.c, np.array(x, copy=True), np.zeros_like(x)
+
+    def gradient(self, sigma):
+        return sigma
+
+    def tangent(self, x, v):
+        return self.K @ v + 12.0 * self.g4 * x ** 2 * v
+
+    def hessp(self, x, v):
+        return self.tangent(x, v)
+
+    dot = staticmethod(_dot)
+
+    @staticmethod
+    def norm(a):
+        return float(np.sqrt(np.dot(a, a)))
+
+
+def _radius_trace(monkeypatch, Rmax, seen):
+    """Run Algorithm 2 on the quartic problem and check every iteration's
+    radius and acceptance against the printed rules; record the branches."""
+    import oracle.solver as S
+
+    radii, bounds, grads = [], [], []
+    real_cg = S.steihaug_cg
+
+    def spy(hv, g, R, tol, max_iter, dot, restart_thr=0.2):
+        p, info = real_cg(hv, g, R, tol, max_iter, dot, restart_thr)
+        radii.append(R)
+        grads.append(np.array(g, copy=True))
+        bounds.append(info["on_boundary"])
+        return p, info
+
+    monkeypatch.setattr(S, "steihaug_cg", spy)
+    rng = np.random.default_rng(28)
+    Q, _ = np.linalg.qr(rng.standard_normal((6, 6)))
+    K = Q @ np.diag([0.2, 0.5, 1.0, 2.0, 3.0, 4.0]) @ Q.T
+    prob = _QuarticProblem(K, 0.2, 3.0 * rng.standard_normal(6))
+    x0 = 2.0 * rng.standard_normal(6)
+    R0, eta_up = 1.0, 0.1
+    prm = TRParams(eta_eq=1e-12, eta_nr=1e-12, eta_cg=1e-10, R0=R0, Rmax=Rmax, eta_up=eta_up, max_nr=60,
+                   max_cg=50)
+    x, _, _, Rend, rep = S.trust_region_step(prob, x0.copy(), None, R0, prm)
+    assert rep.converged
+
+    def W(y):
+        return 0.5 * y @ K @ y + prob.g4 * np.sum(y ** 4) - prob.c @ y
+
+    def grad(y):
+        return K @ y + 4.0 * prob.g4 * y ** 3 - prob.c
+
+    # stress calls: the start, then one trial per Newton iteration
+    trials = prob.stress_calls[1:]
+    assert len(trials) == len(radii) == rep.nr_iters
+    base = x0.copy()
+    R = R0
+    for it, (Rk, xt, onb, gk) in enumerate(zip(radii, trials, bounds, grads)):
+        assert Rk == R, f"iteration {it}: radius {Rk} handed to CG, rules give {R}"
+        # the CG of this iteration starts from the last accepted point
+        np.testing.assert_allclose(gk, grad(base), rtol=0, atol=1e-13)
+        p = xt - base
+        Bp = K @ p + 12.0 * prob.g4 * base ** 2 * p
+        dm = grad(base) @ p + 0.5 * p @ Bp
+        dW = 0.5 * (grad(base) + grad(xt)) @ p
+        rho = dW / dm
+        if rho < 0.25:
+            R = 0.25 * R
+            seen.add("shrink" if rho <= eta_up else "accept_and_shrink")
+        elif rho > 0.75 and onb:
+            seen.add("cap" if 2.0 * R > Rmax else "grow")
+            R = min(2.0 * R, Rmax)
+        else:
+            seen.add("keep_interior" if rho > 0.75 else "keep")
+        if rho > eta_up:
+            base = xt
+            seen.add("accept")
+        else:
+            seen.add("reject" if rho <= 0.0 else "reject_positive")
+    assert Rend == R
+    np.testing.assert_allclose(x, base, atol=0)
+    # the end point is a stationary point of the quartic energy below the start
+    assert np.linalg.norm(grad(x)) < 1e-9
+    assert W(x) < W(x0)
+
+
+def test_trust_region_radius_and_acceptance_rules(monkeypatch):
+    """Algorithm 2's printed rules, checked on scripted traces: R is
+    quartered when rho < 1/4, doubled (capped at R_max) when rho > 3/4 and the
+    step ended on the boundary, kept otherwise, and a step is accepted iff
+    rho > eta_up.  The test records the radius and the gradient handed to
+    every CG solve and the point of every constitutive evaluation, and
+    recomputes rho from Eqs. (18)-(19) with its own quartic energy; the
+    traces together exercise every branch (including 0 < rho <= eta_up and
+    eta_up < rho < 1/4), so a wrong factor or threshold in the oracle fails."""
+    seen = set()
+    for Rmax in (3.5, 3.8):
+        _radius_trace(monkeypatch, Rmax, seen)
+    want = {"shrink", "accept_and_shrink", "grow", "cap", "keep", "keep_interior", "accept", "reject_positive"}
+    assert want <= seen, want - seen

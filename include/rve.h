@@ -52,7 +52,9 @@ typedef enum {
   RVE_ERR_OOM = -3,           /* device allocation failed */
   RVE_ERR_NOT_CONVERGED = -4, /* iteration caps reached */
   RVE_ERR_NONFINITE = -5,     /* NaN/Inf met in a reduction */
-  RVE_ERR_TIMEOUT = -6        /* a bounded device wait gave up */
+  RVE_ERR_TIMEOUT = -6        /* reserved for a bounded device wait that gives
+                                 up; no entry point of this version waits on
+                                 the device without a bound, none returns it */
 } rve_status;
 
 /* One material phase, indexed by the phase id stored per voxel.
@@ -86,6 +88,18 @@ typedef struct {
                          trust-region step; costs 4 B/voxel per product plus
                          C:eps and n on loading voxels, and 13 reals per voxel
                          of storage.  The batched solver keeps the secant. */
+  int passes;         /* 0: FP32 fields use the passes compiled for the axis
+                         lengths 32, 64, 128, 256, 512, 96, 192 and 384
+                         (per axis), with the Steihaug-CG iterate / residual
+                         update fused into the x-inverse pass where Nx is
+                         one of them (default);
+                         1: the generic runtime passes only, with separate
+                         CG update kernels (the same method through a second
+                         implementation, for cross-checks); 2: the compiled
+                         passes with the CG scalars and updates of the
+                         generic path (d.Hd from the stored product, separate
+                         update kernels).  FP64 fields and other lengths
+                         always use the generic passes. */
 } rve_solver_opts;
 
 /* Per-load-step statistics. */
@@ -97,9 +111,21 @@ typedef struct {
   double mean_stress[6], mean_strain[6];
 } rve_step_report;
 
+/* Exit of one Steihaug-CG solve (Algorithm 1), from rve_steihaug. */
+typedef struct {
+  int status;      /* 1 converged (|r| <= eta_cg |g|), 2 boundary (|z| = R,
+                      the non-negative root), 3 negative curvature (d.Hd <= 0:
+                      the root of |z + tau d| = R with the lower model value),
+                      4 max_cg reached, 5 zero right-hand side (z = 0) */
+  int iters;       /* CG iterations (Hessian-vector products of directions) */
+  int hv_products; /* products including the restarts of Eq. (20) */
+  int restarts;    /* Powell restarts (Eq. (20)) */
+} rve_cg_report;
+
 /* Fill opts with defaults: eta_eq 1e-6, eta_nr 0, eta_cg 1e-2, eta_up 0.1,
  * R0 = Rmax = 0 (meaning "10 sqrt(Nvox) |dE|" at the first load step),
- * max_nr 50, max_cg 1000, restart_thr 0.2, precision 32, hessian 0. */
+ * max_nr 50, max_cg 1000, restart_thr 0.2, precision 32, hessian 0,
+ * passes 0. */
 void rve_default_opts(rve_solver_opts* opts);
 
 /* Create a context.  Sec. 2 (cell, strain split), Appendix A (phases).
@@ -183,6 +209,24 @@ rve_status rve_energy_grad(rve_t, const void* p_dev, double* dW_bar_host, double
 rve_status rve_solve_step(rve_t, const double dE_host[6], const uint8_t free_mask_host[6],
                           const void* init_incr_dev, rve_step_report* rep_host);
 
+/* One Steihaug-CG solve (Algorithm 1) at the current state, the
+ * sub-problem of one Newton iteration of Algorithm 2: minimise the quadratic
+ * model m(z) = g : z + 1/2 z : H z over compatible z with |z| <= R, where
+ * g = G : sigma(state) (Eq. (12)) and H the Hessian of Eq. (8) frozen at the
+ * state (secant, or the symmetric consistent tangent with opts.hessian = 1).
+ * z_0 = 0, r_0 = g, d_0 = -r_0; exits on d.Hd <= 0, on |z| reaching R, on
+ * |r| <= eta_cg |g| or after opts.max_cg iterations; Powell restart with
+ * opts.restart_thr (Eq. (20)).  Norms are unnormalised sums over every voxel
+ * and Mandel entry.
+ *  R         trust radius (> 0)
+ *  eta_cg    relative CG tolerance, in (0, 1)
+ *  z_dev     ncomp x Nvox of the context's real type: receives z
+ *  rep_host  may be NULL
+ * The state, the trust radius of the load steps and the options are not
+ * changed.  Synchronises the stream.  RVE_ERR_ARG on a bad R / eta_cg / NULL
+ * z_dev; RVE_ERR_NONFINITE when a CG scalar is not finite. */
+rve_status rve_steihaug(rve_t, double R, double eta_cg, void* z_dev, rve_cg_report* rep_host);
+
 /* One load step solved by L-BFGS instead of the trust-region Newton-CG
  * iteration: the quasi-Newton method that the paper notes becomes usable
  * once the first-order incremental energy (Eq. (18)) stands in for the
@@ -261,7 +305,10 @@ rve_status rve_pass_stats(rve_t, long long* counts_host, double* ms_host, int n)
  * needs to start at zero); calls whose work overlaps on the GPU (different
  * streams, or host threads without ordering) race on it and must be
  * serialised by the caller.  Returns RVE_ERR_ARG (NULL pointer, bad dims,
- * grid over the limit) or RVE_ERR_CUDA; no message is stored. */
+ * grid over the limit) or RVE_ERR_CUDA; no message is stored.  A CUDA error
+ * already pending on the calling thread when the call starts (from earlier
+ * work) makes it return RVE_ERR_CUDA at once, launching nothing and leaving
+ * that error pending for its owner (cudaGetLastError). */
 rve_status rve_project_noalloc(const int dims[3], int ndim, const float* v_dev, float* out_dev,
                                const uint8_t free_mask_host[6], void* stream);
 

@@ -24,7 +24,7 @@ class rve_solver_opts(ctypes.Structure):
     _fields_ = [("eta_eq", ctypes.c_double), ("eta_nr", ctypes.c_double), ("eta_cg", ctypes.c_double),
                 ("eta_up", ctypes.c_double), ("R0", ctypes.c_double), ("Rmax", ctypes.c_double),
                 ("max_nr", ctypes.c_int), ("max_cg", ctypes.c_int), ("restart_thr", ctypes.c_double),
-                ("precision", ctypes.c_int), ("hessian", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("hessian", ctypes.c_int), ("passes", ctypes.c_int)]
 
 
 class rve_step_report(ctypes.Structure):
@@ -32,6 +32,14 @@ class rve_step_report(ctypes.Structure):
                 ("restarts", ctypes.c_int), ("rejected", ctypes.c_int), ("boundary_hits", ctypes.c_int),
                 ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double), ("R", ctypes.c_double),
                 ("mean_stress", ctypes.c_double * 6), ("mean_strain", ctypes.c_double * 6)]
+
+
+class rve_cg_report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("hv_products", ctypes.c_int),
+                ("restarts", ctypes.c_int)]
+
+
+CG_EXIT = {1: "converged", 2: "boundary", 3: "negative_curvature", 4: "max_iter", 5: "zero_rhs"}
 
 
 class RveError(RuntimeError):
@@ -61,6 +69,8 @@ _SIGS = [
     ("rve_solve_step", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_uint8), ctypes.c_void_p,
                                       ctypes.POINTER(rve_step_report)]),
+    ("rve_steihaug", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                    ctypes.POINTER(rve_cg_report)]),
     ("rve_solve_step_lbfgs", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                             ctypes.POINTER(rve_step_report)]),
@@ -218,6 +228,12 @@ def rve_solve_step(h, dE, free_mask=None, init_ptr=0, raise_on_error=True):
     if raise_on_error:
         check(st, h)
     return st, rep
+
+
+def rve_steihaug(h, R, eta_cg, z_ptr):
+    rep = rve_cg_report()
+    check(lib().rve_steihaug(h, float(R), float(eta_cg), ctypes.c_void_p(z_ptr), ctypes.byref(rep)), h)
+    return rep
 
 
 def rve_solve_step_lbfgs(h, dE, free_mask=None, memory=5, max_iter=500, raise_on_error=True):

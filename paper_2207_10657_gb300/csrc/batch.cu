@@ -345,7 +345,8 @@ __global__ void __launch_bounds__(256)
       R Dv = 0, kap = 0;
       if (mt.damaging[ph]) {
         const R kt = kappa_tension<R>(e, nd);
-        const R kk = fmax(khist[d.voff + k], kt);
+        const R khk = khist[d.voff + k];
+        const R kk = kt > khk ? kt : khk;  // keeps a NaN history (fmax would drop it)
         kap = kk;
         Dv = damage_of<R>(kk, mt.kappa0[ph], mt.kappaf[ph]);
       }

@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kCThreads)
       R kt2 = 0;
       for (int c = 0; c < NC; ++c) kt2 += ep[c] * ep[c];
       const R kt = sqrt(kt2), kh = khist[v];
-      const R k = fmax(kh, kt), k0 = mt.kappa0[ph], kf = mt.kappaf[ph];
+      const R k = kt > kh ? kt : kh, k0 = mt.kappa0[ph], kf = mt.kappaf[ph];
       if (kt > kh && k > k0 && k < kf) {
         dpv = kf * k0 / (k * k * (kf - k0));
         const R lam = mt.lam[ph], mu = mt.mu[ph];

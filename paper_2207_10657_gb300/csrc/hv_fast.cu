@@ -476,10 +476,16 @@ template <int N>
 static cudaError_t zproj_n(const GridDesc& g, float2* spec, const SpecWork<float>& w, cudaStream_t st) {
   constexpr int TX = ztx<N>();
   const size_t smem = (size_t)N * 6 * TX * sizeof(float2);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(kf_zproj<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
+  // the attribute is per device: set it once on every device that runs the pass
+  constexpr int kDevs = 64;
+  static bool attr[kDevs] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kDevs || !attr[dev]) {
+    e = cudaFuncSetAttribute(kf_zproj<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kDevs) attr[dev] = true;
   }
   const dim3 grid((g.nxh + TX - 1) / TX, g.ny);
   kf_zproj<N><<<grid, zthreads<N>(), smem, st>>>(spec, g.ny, g.nxh, w.tw[2], w.gdiff[0], w.gavg[0], w.gdiff[1],

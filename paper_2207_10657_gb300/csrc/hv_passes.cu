@@ -191,8 +191,8 @@ static cudaError_t spectral_middle(const GridDesc& g, SpecWork<R>& w, cudaStream
       e = cudaErrorNotSupported;
       PassScope ps(w.timer, st, pass == 0 ? PASS_YFWD : (pass == 1 ? PASS_ZPROJ : PASS_YINV));
       if constexpr (F32) {
-        if (pass != 1 && fast_size(g.ny)) e = fast_ycols(g, w.spec, w.tw[1], pass == 2, st);
-        if (pass == 1 && fast_size(g.nz)) e = fast_zproj(g, w.spec, w, st);
+        if (!w.generic && pass != 1 && fast_size(g.ny)) e = fast_ycols(g, w.spec, w.tw[1], pass == 2, st);
+        if (!w.generic && pass == 1 && fast_size(g.nz)) e = fast_zproj(g, w.spec, w, st);
       }
       if (e == cudaErrorNotSupported) {
         if (pass == 0) k_ycols<R, false><<<yg, kYThreads, ysm, st>>>(w.spec, g, w.ty, w.py, w.tw[1]);
@@ -209,7 +209,7 @@ static cudaError_t spectral_middle(const GridDesc& g, SpecWork<R>& w, cudaStream
     e = cudaErrorNotSupported;
     PassScope ps(w.timer, st, PASS_YPROJ2D);
     if constexpr (F32) {
-      if (fast_size(g.ny)) e = fast_yproj2d(g, w.spec, w, st);
+      if (!w.generic && fast_size(g.ny)) e = fast_yproj2d(g, w.spec, w, st);
     }
     if (e == cudaErrorNotSupported) {
       const dim3 pg((g.nxh + w.tz - 1) / w.tz);
@@ -245,8 +245,8 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
   {
   PassScope ps(w.timer, st, PASS_XFWD);
   if constexpr (F32) {
-    if (fast_size(g.nx)) {
-      const bool want = mode == XIn::Tangent && dot_with != nullptr && dot_with == in;
+    if (!w.generic && fast_size(g.nx)) {
+      const bool want = mode == XIn::Tangent && dot_with != nullptr && dot_with == in && !w.unfused;
       e = fast_xfwd(g, in, phase, damage, mt, w.spec, w.tw[0], mode == XIn::Tangent, want ? w.partials : nullptr,
                     &fwd_blocks, st, &w.cons);
       fwd_dot = want && e == cudaSuccess;
@@ -272,7 +272,7 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
   {
   PassScope ps(w.timer, st, PASS_XINV);
   if constexpr (F32) {
-    if (fast_size(g.nx))
+    if (!w.generic && fast_size(g.nx))
       e = fast_xinv(g, w.spec, out, self ? nullptr : dot_with, w.partials, w.tw[0], dot, self, &nblocks, st);
   }
   if (e == cudaErrorNotSupported) {
@@ -300,7 +300,7 @@ cudaError_t spectral_hv_cg(const GridDesc& g, SpecWork<float>& w, const MatTable
                            const uint8_t* phase, const float* damage, float* z, float* r, double* dHd,
                            cudaError_t (*between)(void*), void* between_arg, const int* status, const double* alpha,
                            const double* tau, double* sums, cudaStream_t st, long long* nlaunch) {
-  if (!fast_size(g.nx)) return cudaErrorNotSupported;
+  if (w.generic || w.unfused || !fast_size(g.nx)) return cudaErrorNotSupported;
   long long nl = 0;
   cudaError_t e;
   int fb = 0, ib = 0;

@@ -41,6 +41,8 @@ template <typename R> struct SpecWork {
   int max_partials = 0;
   PassTimer* timer = nullptr;  // optional per-pass event timing
   ConsTan<R> cons;             // set: tangent passes apply the consistent tangent
+  bool generic = false;        // true: never take the compiled FP32 passes
+  bool unfused = false;        // true: compiled passes, but CG scalars and updates as the generic path
 };
 
 enum class XIn { Plain = 0, Tangent = 1 };

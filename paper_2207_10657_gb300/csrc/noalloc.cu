@@ -85,6 +85,10 @@ extern "C" {
 rve_status rve_project_noalloc(const int dims[3], int ndim, const float* v_dev, float* out_dev,
                                const uint8_t free_mask_host[6], void* stream) {
   if (!dims || !v_dev || !out_dev) return fail(RVE_ERR_ARG, "NULL argument");
+  // An error left pending by earlier, unrelated work on this thread would be
+  // reported by the launch checks below as this call's own; refuse to start
+  // instead, and leave that error for its owner to read.
+  if (cudaPeekAtLastError() != cudaSuccess) return fail(RVE_ERR_CUDA, "an earlier CUDA error is pending");
   if (ndim != 2 && ndim != 3) return fail(RVE_ERR_ARG, "ndim must be 2 or 3");
   for (int a = 0; a < ndim; ++a)
     if (!five_smooth_even(dims[a]))

@@ -166,6 +166,8 @@ rve_status create_impl(rve_ctx* c, const uint8_t* phase_ids, const rve_phase* ph
   }
   CK(spectral_setup<R>(g, m->sw), "spectral setup");
   m->sw.timer = &c->timer;
+  m->sw.generic = c->opts.passes == 1;
+  m->sw.unfused = c->opts.passes == 2;
   const size_t nf = (size_t)g.ncomp * g.nvox * sizeof(R);
   const size_t ns = (size_t)g.nvox * sizeof(R);
   R** fields[] = {&m->eps, &m->sig, &m->sig_t, &m->g, &m->z, &m->r, &m->d, &m->Hd, &m->tmp};
@@ -225,6 +227,7 @@ rve_status steihaug(rve_ctx* c, rve_step_report* rep) {
   CK(cg_init<R>(g, m->g, m->z, m->r, m->d, m->S, m->sw.partials, c->st, nl), "cg init");
   rve_status s = read_scalars<R>(c);
   if (s != RVE_OK) return s;
+  if (c->Sh->status == CG_NONFINITE) return fail(c, RVE_ERR_NONFINITE, "non-finite gradient in CG");
   if (c->Sh->status != CG_RUN) return RVE_OK;
   for (;;) {
     // product, step length and iterate / residual update; on the compiled
@@ -313,6 +316,8 @@ rve_status solve_step_impl(rve_ctx* c, const double dE[6], const void* init, rve
   rve_status s = gradient<R>(c);
   if (s != RVE_OK) return s;
   if ((s = read_scalars<R>(c)) != RVE_OK) return s;
+  if (!std::isfinite(c->Sh->gg) || !std::isfinite(c->Sh->sts))
+    return fail(c, RVE_ERR_NONFINITE, "non-finite stress or gradient at the start of the load step");
   double rel = c->Sh->sts > 0 ? std::sqrt(c->Sh->gg / c->Sh->sts) : 0.0;
   bool converged = rel <= c->opts.eta_eq;
   while (!converged && rp->nr_iters < c->opts.max_nr) {
@@ -417,6 +422,8 @@ rve_status lbfgs_step_impl(rve_ctx* c, const double dE[6], int mem, int max_iter
      "stress");
   if ((s = gradient<R>(c)) != RVE_OK) return s;
   if ((s = read_scalars<R>(c)) != RVE_OK) return s;
+  if (!std::isfinite(c->Sh->gg) || !std::isfinite(c->Sh->sts))
+    return fail(c, RVE_ERR_NONFINITE, "non-finite stress or gradient at the start of the load step");
   double rel = c->Sh->sts > 0 ? std::sqrt(c->Sh->gg / c->Sh->sts) : 0.0;
   std::vector<int> ord;  // pair slots, oldest first
   bool new_pair = false;  // a pair entered since the last direction
@@ -671,6 +678,33 @@ rve_status energy_grad_impl(rve_ctx* c, const void* p, double* dW, double* dm, v
   return RVE_OK;
 }
 
+// Algorithm 1 alone at the state: g = G : sigma(state), then Steihaug CG
+// with radius Rad and relative tolerance eta_cg; the load-step radius and
+// the options are restored afterwards.
+template <typename R>
+rve_status steihaug_once_impl(rve_ctx* c, double Rad, double eta_cg, void* zout, rve_cg_report* rep) {
+  Impl<R>* m = impl_of<R>(c);
+  const double R0 = c->R, eta0 = c->opts.eta_cg;
+  c->R = Rad;
+  c->opts.eta_cg = eta_cg;
+  rve_step_report sr{};
+  rve_status s = gradient<R>(c);
+  if (s == RVE_OK) s = steihaug<R>(c, &sr);
+  c->R = R0;
+  c->opts.eta_cg = eta0;
+  if (s != RVE_OK) return s;
+  CK(cudaMemcpyAsync(zout, m->z, (size_t)c->g.ncomp * c->g.nvox * sizeof(R), cudaMemcpyDeviceToDevice, c->st),
+     "copy z");
+  CK(cudaStreamSynchronize(c->st), "synchronize");
+  if (rep) {
+    rep->status = c->Sh->status;
+    rep->iters = sr.cg_iters;
+    rep->hv_products = sr.hv_products;
+    rep->restarts = sr.restarts;
+  }
+  return RVE_OK;
+}
+
 template <typename R>
 rve_status apply_impl(rve_ctx* c, const void* v, void* out, bool tangent) {
   Impl<R>* m = impl_of<R>(c);
@@ -699,6 +733,7 @@ void rve_default_opts(rve_solver_opts* o) {
   o->restart_thr = 0.2;
   o->precision = 32;
   o->hessian = 0;
+  o->passes = 0;
 }
 
 rve_status rve_create(const int dims[3], int ndim, const uint8_t* phase_ids_dev, const rve_phase* phases, int nphase,
@@ -732,6 +767,10 @@ rve_status rve_create(const int dims[3], int ndim, const uint8_t* phase_ids_dev,
   if (c->opts.hessian != 0 && c->opts.hessian != 1) {
     delete c;
     return fail(nullptr, RVE_ERR_ARG, "hessian must be 0 (secant) or 1 (symmetric consistent)");
+  }
+  if (c->opts.passes < 0 || c->opts.passes > 2) {
+    delete c;
+    return fail(nullptr, RVE_ERR_ARG, "passes must be 0 (compiled, fused CG), 1 (generic) or 2 (compiled, unfused CG)");
   }
   c->precision = c->opts.precision;
   c->st = static_cast<cudaStream_t>(stream);
@@ -830,6 +869,14 @@ rve_status rve_solve_step(rve_t c, const double dE[6], const uint8_t fm[6], cons
     if (s != RVE_OK) return s;
   }
   return DISPATCH(c, solve_step_impl, dE, init, rep);
+}
+
+rve_status rve_steihaug(rve_t c, double R, double eta_cg, void* z, rve_cg_report* rep) {
+  if (!c) return RVE_ERR_ARG;
+  if (!z) return fail(c, RVE_ERR_ARG, "z is NULL");
+  if (!(R > 0.0) || !std::isfinite(R)) return fail(c, RVE_ERR_ARG, "R must be positive and finite");
+  if (!(eta_cg > 0.0 && eta_cg < 1.0)) return fail(c, RVE_ERR_ARG, "eta_cg must be in (0, 1)");
+  return DISPATCH(c, steihaug_once_impl, R, eta_cg, z, rep);
 }
 
 rve_status rve_solve_step_lbfgs(rve_t c, const double dE[6], const uint8_t fm[6], int memory, int max_iter,

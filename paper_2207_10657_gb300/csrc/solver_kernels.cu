@@ -231,7 +231,10 @@ __global__ void __launch_bounds__(kVThreads)
       R D = 0, kap = 0;
       if (mt.damaging[ph]) {
         const R kt = kappa_tension<R>(ev, nd);
-        const R k = fmax(elc<R>(kh4, q), kt);
+        // max(kappa_n, kappa_t) that keeps a NaN history (fmax would drop
+        // it): invalid input then reaches the sums and is reported
+        const R khq = elc<R>(kh4, q);
+        const R k = kt > khq ? kt : khq;
         kap = k;
         D = damage_of<R>(k, mt.kappa0[ph], mt.kappaf[ph]);
       }

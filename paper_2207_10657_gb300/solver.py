@@ -132,6 +132,14 @@ class RVESolver:
         d["status"] = st
         return d
 
+    def steihaug(self, R, eta_cg, out=None):
+        """One Steihaug-CG solve (Algorithm 1) at the state with radius R:
+        returns (z, report dict with the exit reason)."""
+        out = self.field() if out is None else out
+        rep = B.rve_steihaug(self.h, R, eta_cg, self._chk(out))
+        return out, {"reason": B.CG_EXIT.get(rep.status, str(rep.status)), "iters": rep.iters,
+                     "hv_products": rep.hv_products, "restarts": rep.restarts}
+
     def solve_step_lbfgs(self, dE, free_mask=None, memory=5, max_iter=500, raise_on_error=True):
         """One load step by L-BFGS with the first-order incremental energy in
         its line search (report: nr_iters = iterations, cg_iters = line-search

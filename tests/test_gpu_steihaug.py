@@ -1,0 +1,107 @@
+"""One Steihaug-CG solve (Algorithm 1) through the C ABI against the FP64
+oracle's steihaug_cg on the same Hessian and gradient (needs a GB300).
+
+The cases run on axis length 32, where the compiled FP32 passes and the CG
+update fused into the x-inverse pass are used (passes = 0), through the
+compiled passes with separate CG update kernels (passes = 2) and through the
+generic passes (passes = 1); FP64 fields use the generic passes.  The state
+holds a fully damaged band (kappa_n >= kappa_f, D = 1) and a matrix loaded
+into softening, and the radius / Hessian are chosen so that every exit of
+Algorithm 1 is taken: the boundary (positive root of |z + tau d| = R), the
+negative-curvature exit of the symmetric consistent tangent (the root with
+the lower model value), and convergence inside the region.  z is compared
+element by element (relative L2), the exit reason and the iteration count
+exactly.
+
+Tolerances (relative L2 of z): FP64 1e-10; FP32 1e-5 on exits within 8
+iterations and 1e-4 (the spec strain-field bound) on later exits (the
+2D negative-curvature exit after 15 iterations, the converged exits after 26
+and 56): the rounding of the FP32 fields compounds from iteration to
+iteration, as in any FP32 CG, through the compiled and the generic passes
+alike, while the FP64 scalars keep the exit and the iteration count
+identical."""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.consistent import ConsistentRVE
+from oracle.solver import steihaug_cg
+from synth import random_spheres, circular_inclusion, random_field
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+MATRIX = (1.0, 0.3, True, 1e-4, 1e-3)
+STIFF = (10.0, 0.2, False, 0.0, 0.0)
+ETA_CG = 1e-3
+TOL = {32: 1e-5, 64: 1e-10}
+TOL_LONG = {32: 1e-4, 64: 1e-10}  # exits after more than 8 iterations
+
+
+def _state(dims, seed=3):
+    """Phase map, total strain (matrix in softening, uniaxial 3e-4 plus a
+    small compatible fluctuation) and history (a quarter of the cell with
+    kappa_n = 2e-3 >= kappa_f), rounded to FP32 so both sides see the same
+    numbers."""
+    nd = len(dims)
+    shape = tuple(reversed(dims))
+    ncomp = 6 if nd == 3 else 3
+    if nd == 3:
+        pm = random_spheres(dims, count=6, rmin=3.0, rmax=6.0, seed=seed)
+        E = np.array([0, 0, 3e-4, 0, 0, 0.0])
+    else:
+        pm = circular_inclusion(dims, 0.3)
+        E = np.array([3e-4, 0, 0.0])
+    eps = E.reshape((ncomp,) + (1,) * nd) + 2e-5 * oracle.project(random_field(ncomp, dims, seed=seed + 1))
+    kh = np.zeros(shape)
+    kh[(slice(0, shape[0] // 4),) + (slice(None),) * (nd - 1)] = 2e-3
+    return pm, eps.astype(np.float32).astype(np.float64), kh.astype(np.float32).astype(np.float64)
+
+
+# (dims, hessian, R, exit the oracle takes)
+CASES = [
+    ((32, 32), 0, 0.005, "boundary"),
+    ((32, 32), 0, 0.01, "boundary"),
+    ((32, 32), 0, 1.0, "converged"),
+    ((32, 32), 1, 1.0, "negative_curvature"),
+    ((32, 32, 32), 0, 0.05, "boundary"),
+    ((32, 32, 32), 0, 1.0, "converged"),
+    ((32, 32, 32), 1, 0.05, "boundary"),
+    ((32, 32, 32), 1, 10.0, "negative_curvature"),
+]
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_solve(dims, hessian, R):
+    pm, eps, kh = _state(dims)
+    phases = [oracle.Phase(*MATRIX), oracle.Phase(STIFF[0], STIFF[1])]
+    rve = (ConsistentRVE if hessian else oracle.RVE)(pm, phases)
+    sig, aux, _ = rve.stress(eps, kh)
+    g = rve.gradient(sig)
+    z, info = steihaug_cg(lambda v: rve.hessp(aux, v), g, R, ETA_CG * rve.norm(g), 1000, rve.dot)
+    return z, info
+
+
+@pytest.mark.parametrize("precision,passes", [(32, 0), (32, 1), (32, 2), (64, 0)])
+@pytest.mark.parametrize("dims,hessian,R,reason", CASES)
+def test_steihaug_exit_matches_oracle(dims, hessian, R, reason, precision, passes):
+    from paper_2207_10657_gb300 import RVESolver, build
+    build.build()
+    pm, eps, kh = _state(dims)
+    zref, info = _oracle_solve(dims, hessian, R)
+    assert info["reason"] == reason  # the case takes the exit it is meant to
+    dt = np.float32 if precision == 32 else np.float64
+    s = RVESolver(dims, pm, [MATRIX, STIFF], precision=precision, hessian=hessian, passes=passes)
+    s.set_state(torch.from_numpy(eps.astype(dt)).cuda(), torch.from_numpy(kh.astype(dt)).cuda())
+    z, rep = s.steihaug(R, ETA_CG)
+    z = z.cpu().numpy().astype(np.float64)
+    s.close()
+    err = float(np.linalg.norm(z - zref) / np.linalg.norm(zref))
+    assert rep["reason"] == info["reason"], (rep, info)
+    assert rep["iters"] == info["iters"], (rep, info)
+    assert err < (TOL_LONG if info["iters"] > 8 else TOL)[precision], err
+    if reason != "converged":
+        assert abs(np.linalg.norm(z) / R - 1.0) < 10 * TOL[precision]

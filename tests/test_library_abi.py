@@ -52,7 +52,7 @@ def test_default_opts_and_argument_errors(libpath):
     """Host-side paths that need no GPU: defaults and argument validation."""
     from paper_2207_10657_gb300 import binding as B
     o = B.rve_default_opts()
-    assert o.restart_thr == 0.2 and o.precision == 32 and o.max_nr == 50
+    assert o.restart_thr == 0.2 and o.precision == 32 and o.max_nr == 50 and o.hessian == 0 and o.passes == 0
     lib = B.lib()
     h = ctypes.c_void_p()
     dims = (ctypes.c_int * 3)(7, 8, 8)  # odd size is rejected before any CUDA call
@@ -79,7 +79,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    fields = {"rve_phase": B.rve_phase, "rve_solver_opts": B.rve_solver_opts, "rve_step_report": B.rve_step_report}
+    fields = {"rve_phase": B.rve_phase, "rve_solver_opts": B.rve_solver_opts, "rve_step_report": B.rve_step_report,
+              "rve_cg_report": B.rve_cg_report}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rve.h"', "int main(void) {"]
     for s, cls in fields.items():
         lines.append(f'  printf("{s} %zu\\n", sizeof({s}));')

@@ -1,0 +1,292 @@
+// Tile bodies of the compile-time-specialised FP32 passes (hv_fast.cu):
+// one x-forward row tile, one x-inverse row tile, one y column tile.  Sizes
+// are template constants: powers of two from 32 to 512 and 3 * 2^k up to
+// 384.
+#pragma once
+
+#include "fft_fast.cuh"
+#include "hv_passes.cuh"
+
+namespace rve {
+
+
+constexpr int kFT = 256;       // threads of the x / y passes
+constexpr int kFBudget = 4096; // complex elements per x / y block
+
+template <int N, int NC> constexpr int xq() {
+  // voxel rows per x block: NC*Q/2 lines of N, prefer an odd line count
+  constexpr int nlmax = kFBudget / N;
+  constexpr int q0 = (2 * nlmax) / NC;
+  constexpr int q1 = (NC & 1) ? (q0 & ~1) : q0;
+  constexpr int q2 = (q1 < ((NC & 1) ? 2 : 1)) ? ((NC & 1) ? 2 : 1) : q1;
+  constexpr int nl = NC * q2 / 2;
+  return ((nl & 1) == 0 && q2 > ((NC & 1) ? 2 : 1)) ? q2 - ((NC & 1) ? 2 : 1) : q2;
+}
+template <int N> constexpr int ytx() { return (kFBudget / N) < 16 ? (kFBudget / N) : 16; }
+template <int N> constexpr int ztx() { return N <= 64 ? 16 : 4; }
+template <int N> constexpr int zthreads() { return N >= 512 ? 512 : 256; }
+template <int N> constexpr int zminblocks() { return N >= 512 ? 1 : 3; }
+template <int N> constexpr int p2tx() { return (kFBudget / (3 * N)) < 16 ? (kFBudget / (3 * N)) : 16; }
+
+// ------------------------------------------------------------ x forward
+// One x-forward tile: the voxel rows [row0, row_end) (at most xq rows),
+// tangent applied on load, forward FFT of the real rows packed in pairs,
+// half spectrum stored.  Returns this thread's share of in : (tangent : in)
+// (MODE >= 1).  `buf` holds NC * xq / 2 lines of N.
+template <int N, int NC, int MODE>
+__device__ __forceinline__ float xfwd_rows(float2* buf, const float* __restrict__ in,
+                                           const uint8_t* __restrict__ phase, const float* __restrict__ dmg,
+                                           const MatTable<float>& mt, float2* __restrict__ spec,
+                                           const long long nrows, const long long nvox,
+                                           const float2* __restrict__ tw, const long long row0,
+                                           const long long row_end, const float* __restrict__ cdp,
+                                           const float* __restrict__ ca, const float* __restrict__ cn) {
+  constexpr int Q = xq<N, NC>();
+  constexpr int NL = NC * Q / 2;
+  constexpr int ND = NC == 6 ? 3 : 2;
+  float acc = 0.f;  // in : (tangent : in) over this thread's few voxels (MODE >= 1)
+  // one voxel per thread per step: consecutive threads take consecutive x,
+  // so the line-interleaved shared-memory writes are (nearly) conflict free
+  constexpr int ITEMS = Q * N;
+  constexpr int STEPS = (ITEMS + kFT - 1) / kFT;
+  constexpr int BATCH = STEPS < 4 ? STEPS : 4;
+  for (int s0 = 0; s0 < STEPS; s0 += BATCH) {
+    float v[BATCH][NC];
+#pragma unroll
+    for (int b = 0; b < BATCH; ++b) {
+      const int idx = threadIdx.x + (s0 + b) * kFT;
+      const int q = idx / N, x = idx - (idx / N) * N;
+      const long long row = row0 + q;
+      const bool ok = (s0 + b < STEPS) && idx < ITEMS && row < row_end;
+      const long long vox = row * N + x;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) v[b][c] = ok ? __ldg(in + c * nvox + vox) : 0.f;
+      if (MODE >= 1 && ok) {
+        const float keep = 1.f - __ldg(dmg + vox);
+        const int ph = __ldg(phase + vox);
+        const float lam = mt.lam[ph] * keep, tmu = 2.f * mt.mu[ph] * keep;
+        float tr = 0.f;
+#pragma unroll
+        for (int i = 0; i < ND; ++i) tr += v[b][i];
+        float hdp = 0.f, nv = 0.f, av = 0.f;
+        if constexpr (MODE == 2) {
+          hdp = 0.5f * __ldg(cdp + vox);
+          if (hdp != 0.f) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+              nv += __ldg(cn + c * nvox + vox) * v[b][c];
+              av += __ldg(ca + c * nvox + vox) * v[b][c];
+            }
+          }
+        }
+        float dv = 0.f;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          float sg = tmu * v[b][c] + (c < ND ? lam * tr : 0.f);
+          if constexpr (MODE == 2) {
+            if (hdp != 0.f) sg -= hdp * (__ldg(ca + c * nvox + vox) * nv + __ldg(cn + c * nvox + vox) * av);
+          }
+          dv += v[b][c] * sg;
+          v[b][c] = sg;
+        }
+        acc += dv;
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < BATCH; ++b) {
+      const int idx = threadIdx.x + (s0 + b) * kFT;
+      if (s0 + b < STEPS && idx < ITEMS) {
+        const int q = idx / N, x = idx - (idx / N) * N;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int rho = q * NC + c;
+          reinterpret_cast<float*>(&buf[x * NL + (rho >> 1)])[rho & 1] = v[b][c];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  fft_ct<N, NL, kFT, false>(buf, tw);
+  constexpr int NXH = N / 2 + 1;
+  for (int idx = threadIdx.x; idx < NL * NXH; idx += kFT) {
+    const int p = idx / NXH, k = idx - (idx / NXH) * NXH;
+    const float2 zk = buf[k * NL + p];
+    const float2 zm = buf[((N - k) % N) * NL + p];
+    const float2 xa = make_float2((zk.x + zm.x) * 0.5f, (zk.y - zm.y) * 0.5f);
+    const float2 xb = make_float2((zk.y + zm.y) * 0.5f, (zm.x - zk.x) * 0.5f);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int rho = 2 * p + h;
+      const int q = rho / NC, c = rho - (rho / NC) * NC;
+      const long long row = row0 + q;
+      if (row < row_end) spec[(c * nrows + row) * NXH + k] = h ? xb : xa;
+    }
+  }
+  return acc;
+}
+
+// ------------------------------------------------------------ x inverse
+// CG: instead of storing the product Hd, apply the CG iterate / residual
+// update of Algorithm 1 with it (status, alpha and tau read from the device
+// scalars): running, z += alpha d and r += alpha Hd with the sums r'.r',
+// r'.r and z'.z per block in partials[3 b + s]; on a boundary or
+// negative-curvature exit, z += tau d.
+// One x-inverse tile: rows [row0, row_end); its block sums go to
+// partials[pidx] (DOT) or partials[3 pidx + s] (CG).  L2LOAD: the spectrum
+// was written by other blocks of the same launch, so it is read through L2
+// (ld.global.cg), never from a stale L1 line.  `red` holds 3 * 32 doubles.
+template <int N, int NC, bool DOT, bool CG, bool L2LOAD>
+__device__ __forceinline__ void xinv_rows(float2* buf, double* red, const float2* __restrict__ spec,
+                                          float* __restrict__ out, const float* __restrict__ dotw,
+                                          double* __restrict__ partials, const long long nrows,
+                                          const long long nvox, const float2* __restrict__ tw, const float scale,
+                                          const bool self_dot, float* __restrict__ cz, float* __restrict__ cr,
+                                          const float* __restrict__ cd, const int* __restrict__ cstatus,
+                                          const double* __restrict__ calpha, const double* __restrict__ ctau,
+                                          const long long row0, const long long row_end, const long long pidx) {
+  constexpr int Q = xq<N, NC>();
+  constexpr int NL = NC * Q / 2;
+  constexpr int NXH = N / 2 + 1;
+  constexpr int HALF = N / 2;
+  // each half-spectrum entry kk of the two real lines packed in line p is
+  // read once and fills both buf[kk] and buf[N - kk] (Hermitian symmetry)
+  constexpr int LITEMS = NL * NXH;
+  constexpr int LSTEPS = (LITEMS + kFT - 1) / kFT;
+  constexpr int LB = LSTEPS < 4 ? LSTEPS : 4;
+  for (int s0 = 0; s0 < LSTEPS; s0 += LB) {
+    float2 xh[LB][2];
+#pragma unroll
+    for (int b = 0; b < LB; ++b) {
+      const int idx = threadIdx.x + (s0 + b) * kFT;
+      const int p = idx / NXH, kk = idx - (idx / NXH) * NXH;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int rho = 2 * p + h;
+        const int q = rho / NC, c = rho - (rho / NC) * NC;
+        const long long row = row0 + q;
+        const float2* src = spec + (c * nrows + row) * NXH + kk;
+        xh[b][h] = (s0 + b < LSTEPS && idx < LITEMS && row < row_end) ? (L2LOAD ? __ldcg(src) : *src)
+                                                                      : make_float2(0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < LB; ++b) {
+      const int idx = threadIdx.x + (s0 + b) * kFT;
+      if (s0 + b < LSTEPS && idx < LITEMS) {
+        const int p = idx / NXH, kk = idx - (idx / NXH) * NXH;
+        float2 a = xh[b][0], c2 = xh[b][1];
+        if (kk == 0 || kk == HALF) {
+          a.y = 0.f;
+          c2.y = 0.f;
+        }
+        buf[kk * NL + p] = make_float2(a.x - c2.y, a.y + c2.x);
+        if (kk != 0 && kk != HALF) buf[(N - kk) * NL + p] = make_float2(a.x + c2.y, c2.x - a.y);
+      }
+    }
+  }
+  __syncthreads();
+  fft_ct<N, NL, kFT, true>(buf, tw);
+  if constexpr (CG) {
+    const int status = *cstatus;
+    const bool run = status == 0, exit_tau = status == 2 || status == 3;  // running / boundary, negative curvature
+    const float al = (float)*calpha, ta = (float)*ctau;
+    KSum<float> cs[3];
+    constexpr int SITEMS = Q * NC * N;
+    constexpr int SSTEPS = (SITEMS + kFT - 1) / kFT;
+    constexpr int SB = SSTEPS < 4 ? SSTEPS : 4;
+    for (int s0 = 0; s0 < SSTEPS; s0 += SB) {
+      float o[SB], zv[SB], rv[SB], dv[SB];
+      long long off[SB];
+      bool ok[SB];
+#pragma unroll
+      for (int b = 0; b < SB; ++b) {
+        const int idx = threadIdx.x + (s0 + b) * kFT;
+        const int rho = idx / N, x = idx - (idx / N) * N;
+        const int q = rho / NC, c = rho - (rho / NC) * NC;
+        const long long row = row0 + q;
+        ok[b] = (s0 + b < SSTEPS) && idx < SITEMS && row < row_end && (run || exit_tau);
+        off[b] = c * nvox + row * N + x;
+        o[b] = ok[b] ? reinterpret_cast<const float*>(&buf[x * NL + (rho >> 1)])[rho & 1] * scale : 0.f;
+        zv[b] = ok[b] ? cz[off[b]] : 0.f;
+        dv[b] = ok[b] ? __ldg(cd + off[b]) : 0.f;
+        rv[b] = (ok[b] && run) ? cr[off[b]] : 0.f;
+      }
+#pragma unroll
+      for (int b = 0; b < SB; ++b) {
+        if (!ok[b]) continue;
+        if (run) {
+          const float zn = zv[b] + al * dv[b], rn = rv[b] + al * o[b];
+          cz[off[b]] = zn;
+          cr[off[b]] = rn;
+          cs[0].add(rn * rn);
+          cs[1].add(rn * rv[b]);
+          cs[2].add(zn * zn);
+        } else {
+          cz[off[b]] = zv[b] + ta * dv[b];
+        }
+      }
+    }
+    double v3[3] = {cs[0].value(), cs[1].value(), cs[2].value()};
+    block_sum<3>(v3, red);
+    if (threadIdx.x == 0)
+      for (int k = 0; k < 3; ++k) partials[3 * pidx + k] = v3[k];
+    return;
+  }
+  KSum<float> acc;
+  constexpr int SITEMS = Q * NC * N;
+  constexpr int SSTEPS = (SITEMS + kFT - 1) / kFT;
+  constexpr int SB = SSTEPS < 8 ? SSTEPS : 8;
+  for (int s0 = 0; s0 < SSTEPS; s0 += SB) {
+    float o[SB], w[SB];
+    long long off[SB];
+    bool ok[SB];
+#pragma unroll
+    for (int b = 0; b < SB; ++b) {
+      const int idx = threadIdx.x + (s0 + b) * kFT;
+      const int rho = idx / N, x = idx - (idx / N) * N;
+      const int q = rho / NC, c = rho - (rho / NC) * NC;
+      const long long row = row0 + q;
+      ok[b] = (s0 + b < SSTEPS) && idx < SITEMS && row < row_end;
+      off[b] = c * nvox + row * N + x;
+      o[b] = ok[b] ? reinterpret_cast<const float*>(&buf[x * NL + (rho >> 1)])[rho & 1] * scale : 0.f;
+      w[b] = (DOT && ok[b]) ? (self_dot ? o[b] : __ldg(dotw + off[b])) : 0.f;
+    }
+#pragma unroll
+    for (int b = 0; b < SB; ++b) {
+      if (ok[b]) {
+        out[off[b]] = o[b];
+        if (DOT) acc.add(o[b] * w[b]);
+      }
+    }
+  }
+  if (DOT) {
+    double v[1] = {acc.value()};
+    block_sum<1>(v, red);
+    if (threadIdx.x == 0) partials[pidx] = v[0];
+  }
+}
+
+// ------------------------------------------------------------ y columns
+// One y tile: columns [kx0, kx0 + ytx) of the plane whose first row is
+// `plane` (row index (c Nz + z) Ny), transformed in place.  L2LOAD as for
+// xinv_rows.
+template <int N, bool INV, bool L2LOAD>
+__device__ __forceinline__ void ycols_tile(float2* buf, float2* __restrict__ spec, const long long plane,
+                                           const int kx0, const int nxh, const float2* __restrict__ tw) {
+  constexpr int TX = ytx<N>();
+  const int tv = min(TX, nxh - kx0);
+  // the first stage reads the columns straight from global memory and the
+  // last one writes them back: no staging through shared memory
+  auto load = [&](int t, int y) -> float2 {
+    const float2* src = spec + (plane + y) * nxh + kx0 + t;
+    return t < tv ? (L2LOAD ? __ldcg(src) : *src) : make_float2(0.f, 0.f);
+  };
+  auto store = [&](int t, int y, float2 v) {
+    if (t < tv) spec[(plane + y) * nxh + kx0 + t] = v;
+  };
+  fft_stage0_from<N, TX, kFT, INV>(buf, load);
+  fft_ct_range<N, TX, kFT, INV, 1, fft_nstages(N) - 1>(buf, tw);
+  fft_stage_last_to<N, TX, kFT, INV>(buf, tw, store);
+}
+
+}  // namespace rve

@@ -277,7 +277,10 @@ rve_status rve_effective_stiffness(rve_t, double tol, int max_cg, double* Cbar_h
  * 5 2D y-FFT + projection + inverse, 6 constitutive trial evaluation,
  * 7 CG vector updates.  rve_pass_timing(h, 1) starts (and resets) the
  * recording of CUDA events on the context's stream around every launch of
- * those kernels (up to 8192 launches; later ones are not timed);
+ * those kernels (up to 8192 launches; later ones are not timed; while it is
+ * on, the host steps the Steihaug-CG iterations one at a time, since events
+ * cannot be recorded inside the device-side loop -- same kernels, same
+ * results);
  * rve_pass_timing(h, 0) stops it.  rve_pass_stats synchronises on the last
  * event and writes, for pass ids 0..n-1, the number of timed launches and
  * their summed device time in milliseconds. */
@@ -432,6 +435,13 @@ const char* rve_last_error(rve_t);
  * context since creation (counters for benchmarks). */
 long long rve_hv_count(rve_t);
 long long rve_launch_count(rve_t);
+/* Number of times this context waited on its stream to read the device
+ * scalars that steer Algorithms 1 and 2 (a counter for benchmarks).  The
+ * Steihaug-CG iterations run on the device as a CUDA graph whose WHILE node
+ * repeats the iteration until an exit or a restart, so a solve waits about
+ * twice plus once per restart, not once per iteration; with per-pass timing
+ * on (rve_pass_timing) the host steps the iterations and waits after each. */
+long long rve_sync_count(rve_t);
 
 /* Free the context and its workspaces.  NULL is ignored. */
 void rve_destroy(rve_t);

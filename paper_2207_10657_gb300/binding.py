@@ -125,6 +125,7 @@ _SIGS = [
     ("rve_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("rve_hv_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("rve_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("rve_sync_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("rve_destroy", None, [ctypes.c_void_p]),
 ]
 
@@ -438,6 +439,10 @@ def rve_last_error(h):
 
 def rve_hv_count(h):
     return lib().rve_hv_count(h)
+
+
+def rve_sync_count(h):
+    return lib().rve_sync_count(h)
 
 
 def rve_launch_count(h):

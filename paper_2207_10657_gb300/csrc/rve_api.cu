@@ -71,10 +71,27 @@ bool five_smooth_even(int n) {
 
 }  // namespace
 
+// One instantiated graph of the device-side Steihaug loop (see
+// steihaug_graph) and what it was captured with.
+struct CgGraph {
+  cudaGraphExec_t exec = nullptr;
+  const void* D = nullptr;    // damage field of the products
+  const void* cdp = nullptr;  // consistent-tangent data (NULL: secant)
+  unsigned free_mask = 0;
+  long long per_iter = 0;     // kernel launches per iteration
+  long long used = 0;         // last use, for replacement
+};
+constexpr int kCgGraphs = 4;
+
 struct rve_ctx {
   int precision = 32;
   GridDesc g{};
   cudaStream_t st = nullptr;
+  cudaStream_t cap = nullptr;  // private stream the Steihaug graphs are captured on
+  CgGraph cg_graph[kCgGraphs];
+  long long cg_graph_clock = 0;
+  bool cg_graph_ok = true;     // false after a graph could not be built: host-driven loop
+  long long host_syncs = 0;    // stream synchronisations that read device scalars
   std::string err = "no error";
   long long hv = 0, launches = 0;
   rve_solver_opts opts{};
@@ -132,6 +149,7 @@ rve_status read_scalars(rve_ctx* c) {
   Impl<R>* m = impl_of<R>(c);
   CK(cudaMemcpyAsync(c->Sh, m->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->st), "read scalars");
   CK(cudaStreamSynchronize(c->st), "synchronize");
+  ++c->host_syncs;
   return RVE_OK;
 }
 
@@ -214,8 +232,118 @@ static cudaError_t launch_alpha(void* p) {
   return cg_alpha(a->S, a->st, a->nl);
 }
 
+// One iteration of Algorithm 1 after the direction d is known: the product
+// H d with the step length and the iterate / residual update (fused into
+// the compiled FP32 passes, else the generic product, step length and
+// update kernels), the residual scalars and the next direction.
+template <typename R>
+cudaError_t issue_cg_iteration(rve_ctx* c, cudaStream_t st, long long* nl) {
+  Impl<R>* m = impl_of<R>(c);
+  const GridDesc& g = c->g;
+  cudaError_t e = cudaErrorNotSupported;
+  if constexpr (std::is_same<R, float>::value) {
+    AlphaArg aa{m->S, st, nl};
+    e = spectral_hv_cg(g, m->sw, m->mt, m->d, m->phase, m->D, m->z, m->r, &m->S->dHd, launch_alpha, &aa,
+                       &m->S->status, &m->S->alpha, &m->S->tau, &m->S->rr_new, st, nl);
+  }
+  if (e == cudaErrorNotSupported) {
+    e = spectral_apply<R>(g, m->sw, m->mt, m->d, m->phase, m->D, XIn::Tangent, m->Hd, m->d, &m->S->dHd, st, nl);
+    if (e == cudaSuccess) e = cg_alpha(m->S, st, nl);
+    if (e == cudaSuccess) {
+      PassScope ps(&c->timer, st, PASS_CGVEC);
+      e = cg_update<R>(g, m->z, m->r, m->d, m->Hd, m->S, m->sw.partials, st, nl);
+    }
+  }
+  if (e == cudaSuccess) e = cg_beta(m->S, st, nl);
+  if (e == cudaSuccess) {
+    PassScope ps(&c->timer, st, PASS_CGVEC);
+    e = cg_dupdate<R>(g, m->z, m->r, m->d, m->S, m->sw.partials, st, nl);
+  }
+  return e;
+}
+
+// The loop condition of the device-side Steihaug loop: continue while the
+// iteration runs and no restart (Eq. (20)) is pending.
+__global__ void k_cg_cond(cudaGraphConditionalHandle h, const DevScalars* S) {
+  cudaGraphSetConditional(h, (S->status == CG_RUN && !S->restart) ? 1u : 0u);
+}
+
+// Capture Algorithm 1's iteration as the body of a graph WHILE node.
+template <typename R>
+cudaError_t build_cg_graph(rve_ctx* c, CgGraph* out) {
+  Impl<R>* m = impl_of<R>(c);
+  cudaError_t e;
+  if (!c->cap && (e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  cudaGraph_t g = nullptr;
+  if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
+  long long nl = 0;
+  if (e == cudaSuccess) {
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      e = issue_cg_iteration<R>(c, c->cap, &nl);
+      if (e == cudaSuccess) {
+        k_cg_cond<<<1, 1, 0, c->cap>>>(h, m->S);
+        e = cudaGetLastError();
+        ++nl;
+      }
+      cudaGraph_t got = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(c->cap, &got);
+      if (e == cudaSuccess) e = e2;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&out->exec, g, 0);
+  cudaGraphDestroy(g);
+  out->per_iter = nl;
+  return e;
+}
+
+// The graph for the current product operands (damage field, consistent
+// tangent, mixed-control mask), built on first use and kept.
+template <typename R>
+CgGraph* cg_graph_for(rve_ctx* c) {
+  Impl<R>* m = impl_of<R>(c);
+  ++c->cg_graph_clock;
+  CgGraph* victim = &c->cg_graph[0];
+  for (CgGraph& gr : c->cg_graph) {
+    if (gr.exec && gr.D == m->D && gr.cdp == m->sw.cons.dp && gr.free_mask == m->sw.free_mask) {
+      gr.used = c->cg_graph_clock;
+      return &gr;
+    }
+    if (!gr.exec || gr.used < victim->used) victim = &gr;
+  }
+  if (victim->exec) cudaGraphExecDestroy(victim->exec);
+  *victim = CgGraph{};
+  if (build_cg_graph<R>(c, victim) != cudaSuccess) {
+    if (victim->exec) cudaGraphExecDestroy(victim->exec);
+    *victim = CgGraph{};
+    cudaGetLastError();  // the failed build leaves no pending error behind
+    c->cg_graph_ok = false;
+    return nullptr;
+  }
+  victim->D = m->D;
+  victim->cdp = m->sw.cons.dp;
+  victim->free_mask = m->sw.free_mask;
+  victim->used = c->cg_graph_clock;
+  return victim;
+}
+
 // Steihaug CG on H p = -g inside radius S.R (Algorithm 1).  Result in z,
-// exit status in S.status.
+// exit status in S.status.  The iterations run on the device, as a graph
+// whose WHILE node repeats the iteration until an exit of Algorithm 1 or a
+// restart: the host synchronises once per restart and once at the end
+// instead of once per iteration.  With per-pass timing on (events cannot be
+// recorded inside a conditional body), or if the graph cannot be built,
+// the host drives the same iteration one launch sequence at a time.
 template <typename R>
 rve_status steihaug(rve_ctx* c, rve_step_report* rep) {
   Impl<R>* m = impl_of<R>(c);
@@ -229,40 +357,27 @@ rve_status steihaug(rve_ctx* c, rve_step_report* rep) {
   if (s != RVE_OK) return s;
   if (c->Sh->status == CG_NONFINITE) return fail(c, RVE_ERR_NONFINITE, "non-finite gradient in CG");
   if (c->Sh->status != CG_RUN) return RVE_OK;
+  CgGraph* gr = (c->cg_graph_ok && !c->timer.on) ? cg_graph_for<R>(c) : nullptr;
   for (;;) {
-    // product, step length and iterate / residual update; on the compiled
-    // FP32 x passes as one fused sequence that never stores H d
-    bool fused = false;
-    if constexpr (std::is_same<R, float>::value) {
-      AlphaArg aa{m->S, c->st, nl};
-      const cudaError_t e = spectral_hv_cg(g, m->sw, m->mt, m->d, m->phase, m->D, m->z, m->r, &m->S->dHd,
-                                           launch_alpha, &aa, &m->S->status, &m->S->alpha, &m->S->tau,
-                                           &m->S->rr_new, c->st, nl);
-      if (e == cudaSuccess) fused = true;
-      else if (e != cudaErrorNotSupported) CK(e, "hessp (fused CG)");
+    const int it0 = c->Sh->iters;
+    if (gr) {
+      CK(cudaGraphLaunch(gr->exec, c->st), "graph launch");
+    } else {
+      CK(issue_cg_iteration<R>(c, c->st, nl), "cg iteration");
     }
-    if (!fused) {
-      CK(spectral_apply<R>(g, m->sw, m->mt, m->d, m->phase, m->D, XIn::Tangent, m->Hd, m->d, &m->S->dHd, c->st,
-                           nl),
-         "hessp");
-      CK(cg_alpha(m->S, c->st, nl), "cg alpha");
-      PassScope ps(&c->timer, c->st, PASS_CGVEC);
-      CK(cg_update<R>(g, m->z, m->r, m->d, m->Hd, m->S, m->sw.partials, c->st, nl), "cg update");
-    }
-    ++c->hv;
-    if (rep) ++rep->hv_products;
-    CK(cg_beta(m->S, c->st, nl), "cg beta");
-    s = read_scalars<R>(c);
-    if (s != RVE_OK) return s;
+    if ((s = read_scalars<R>(c)) != RVE_OK) return s;
+    const int done = c->Sh->iters - it0;
+    c->hv += done;
+    if (gr) c->launches += 1 + done * gr->per_iter;
+    if (rep) rep->hv_products += done;
     if (c->Sh->status != CG_RUN) break;
     if (c->Sh->restart) {
+      // Eq. (20): r = H z + g, beta = 0, then the direction
       CK(spectral_apply<R>(g, m->sw, m->mt, m->z, m->phase, m->D, XIn::Tangent, m->tmp, nullptr, nullptr, c->st, nl),
          "hessp (restart)");
       ++c->hv;
       if (rep) ++rep->hv_products;
       CK(cg_restart<R>(g, m->r, m->tmp, m->g, m->S, m->sw.partials, c->st, nl), "cg restart");
-    }
-    {
       PassScope ps(&c->timer, c->st, PASS_CGVEC);
       CK(cg_dupdate<R>(g, m->z, m->r, m->d, m->S, m->sw.partials, c->st, nl), "cg direction");
     }
@@ -926,6 +1041,7 @@ const char* rve_last_error(rve_t c) { return c ? c->err.c_str() : g_create_error
 
 long long rve_hv_count(rve_t c) { return c ? c->hv : 0; }
 long long rve_launch_count(rve_t c) { return c ? c->launches : 0; }
+long long rve_sync_count(rve_t c) { return c ? c->host_syncs : 0; }
 
 void rve_destroy(rve_t c) {
   if (!c) return;
@@ -934,6 +1050,9 @@ void rve_destroy(rve_t c) {
     else impl_free(impl_of<double>(c));
   }
   if (c->Sh) cudaFreeHost(c->Sh);
+  for (CgGraph& gr : c->cg_graph)
+    if (gr.exec) cudaGraphExecDestroy(gr.exec);
+  if (c->cap) cudaStreamDestroy(c->cap);
   c->timer.destroy();
   delete c;
 }

@@ -150,6 +150,11 @@ template <typename R>
 __global__ void __launch_bounds__(kVThreads)
     k_cg_dupdate(long long n, const R* __restrict__ z, const R* __restrict__ r, R* __restrict__ d,
                  const DevScalars* __restrict__ S, double* __restrict__ part) {
+  // Algorithm 1 continues only while running without a pending restart: a
+  // device-side loop reaches this kernel after every iteration, the host
+  // loop only in that case.  (Skipped, the sums of group D go stale; they
+  // are recomputed by the update after the restart and unused on exit.)
+  if (S->status != CG_RUN || S->restart) return;
   const R beta = (R)S->beta;
   KSum<R> acc[3];
   const long long n4 = n / 4;

@@ -162,6 +162,11 @@ class RVESolver:
     def launch_count(self):
         return B.rve_launch_count(self.h)
 
+    @property
+    def sync_count(self):
+        """Host waits that read the device scalars (counter)."""
+        return B.rve_sync_count(self.h)
+
     def close(self):
         if getattr(self, "h", None) is not None:
             B.rve_destroy(self.h)

@@ -87,16 +87,18 @@ def _args():
     p.add_argument("--n", type=int, default=N, help="grid size (default 256)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default="rve256",
-                   choices=["rve256", "asr", "lbfgs", "onset", "batch96", "warmstart", "hv"],
+                   choices=["rve256", "asr", "lbfgs", "onset", "batch96", "warmstart", "hv", "control"],
                    help="rve256: the 256^3 sphere cell (default); asr: the same cell as an ASR-like "
                         "aggregate / paste / gel model loaded by gel eigenstrain; lbfgs: the default load step "
                         "solved by L-BFGS and by trust-region Newton-CG; onset: a load step at the onset of "
                         "damage with the secant and the symmetric consistent Hessian; batch96: 96 cells of "
                         "uneven sizes; "
                         "warmstart: train the spectral neural operator, then learned vs plain load steps; "
-                        "hv: Hessian-vector products alone (damage snapshot, compatible input), several sizes")
+                        "hv: Hessian-vector products alone (damage snapshot, compatible input), several sizes; "
+                        "control: device-side vs host-stepped Steihaug-CG control at 32^2 and 128^3")
     p.add_argument("--lbfgs-memory", type=int, default=5, help="lbfgs: (s, y) pairs kept")
     p.add_argument("--hv-sizes", default="128,256,384", help="hv: cube edge lengths")
+    p.add_argument("--onset-sizes", default="128,256", help="onset: cube edge lengths")
     p.add_argument("--hv-precisions", default="32,64", help="hv: 32 and / or 64")
     p.add_argument("--ws-train-seconds", type=float, default=120.0,
                    help="warmstart: time budget of the training-data generation (plain solves at 64^3)")
@@ -675,8 +677,69 @@ def run_lbfgs(args):
     return 0
 
 
-ONSET_WORKLOAD = ("128^3 random-sphere cell (48 spheres, r~U[4,10], seed 0; the materials of the load-step "
-                  "workload), uniaxial eps_zz (other components stress-free): after a first increment of 5e-5 "
+def run_control(args):
+    """Host-wait cost of Algorithm 1's control: the same load steps with the
+    Steihaug iterations as device-side graph loops and stepped from the host
+    (rve_set_device_loop), on the 2D configuration-1 cell (32^2 plane strain,
+    centred inclusion, the first three increments of 1e-4, FP32) and on the
+    128^3 sphere cell (the default first increment, FP32)."""
+    import numpy as np
+    import torch
+    from paper_2207_10657_gb300 import RVESolver, binding, build as _build
+    from synth import circular_inclusion, random_spheres
+    _build.build()
+    st = torch.cuda.Stream()
+    cases = []
+    pm2 = circular_inclusion((32, 32), 0.3)
+    R2 = 10 * np.sqrt(32 * 32) * 1e-4
+    cases.append(("2D 32^2 plane strain, centred inclusion (vol. frac 0.3), eps_xx += 1e-4 three times from "
+                  "the unloaded cell, other components stress-free",
+                  (32, 32), pm2, [MATRIX, (10.0, 0.3, False, 0.0, 0.0)], [[1e-4, 0, 0]] * 3, [0, 1, 1],
+                  dict(R0=R2, Rmax=R2, max_nr=400, max_cg=500)))
+    pm3 = random_spheres((128, 128, 128), count=48, rmin=4.0, rmax=10.0, seed=0)
+    cases.append(("128^3 sphere cell (48 spheres), the default first increment eps_zz += 5e-5",
+                  (128, 128, 128), pm3, [MATRIX, STIFF], [[0, 0, INC, 0, 0, 0]], FREE, dict(max_nr=400)))
+    out = []
+    for name, dims, pm, phases, incs, free, opts in cases:
+        res = {}
+        for mode in ("device", "host"):
+            # a fresh context per mode: the trust radius carries over between load steps
+            with torch.cuda.stream(st):
+                s = RVESolver(dims, pm, phases, precision=32, stream=st, eta_eq=1e-6, eta_cg=1e-2, **opts)
+                eps0 = s.field(0.0)
+            binding.rve_set_device_loop(s.h, mode == "device")
+
+            def path():
+                s.set_state(eps0)
+                return [s.solve_step(dE, free_mask=free, raise_on_error=False) for dE in incs]
+
+            for _ in range(args.warmup):
+                path()
+            torch.cuda.synchronize()
+            y0 = s.sync_count
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(st)
+            reps = [path() for _ in range(args.steps)]
+            ev1.record(st)
+            torch.cuda.synchronize()
+            cg = sum(r["cg_iters"] for rr in reps for r in rr)
+            res[mode] = {"ms_per_path": ev0.elapsed_time(ev1) / args.steps,
+                         "host_waits_per_path": (s.sync_count - y0) / args.steps, "cg_iters_per_path": cg / args.steps}
+            s.close()
+        d, h = res["device"], res["host"]
+        out.append({"case": name, "device_loop": d, "host_stepped": h,
+                    "host_overhead_us_per_cg_iteration": 1e3 * (h["ms_per_path"] - d["ms_per_path"])
+                    / max(d["cg_iters_per_path"], 1)})
+    line = {"metric": "load-path time with device-side vs host-stepped Steihaug-CG control",
+            "value": out[0]["device_loop"]["ms_per_path"], "unit": "ms per load path (32^2 case)", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": "control", "cases": out}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+ONSET_WORKLOAD = ("random-sphere cells (48 spheres at 128^3, 144 at 256^3, r~U[4,10], seed 0; the materials of the "
+                  "load-step workload), uniaxial eps_zz (other components stress-free): after a first increment of 5e-5 "
                   "(damage starts), a step = the next increment of 5e-6 from that state (reset every step), "
                   "trust-region Newton + Steihaug CG to rel. residual 1e-6, with the secant Hessian and with the "
                   "symmetric consistent tangent")
@@ -685,55 +748,72 @@ ONSET_WORKLOAD = ("128^3 random-sphere cell (48 spheres, r~U[4,10], seed 0; the 
 def run_onset(args):
     """One load step at the damage onset with the secant and with the
     symmetric consistent Hessian (the converged state of a first increment
-    is the reference state of every timed step)."""
+    is the reference state of every timed step), on the sphere cells of
+    --onset-sizes (48 spheres at 128^3, 144 at 256^3, r ~ U[4, 10])."""
     import torch
     from paper_2207_10657_gb300 import RVESolver, build as _build
     from synth import random_spheres
     _build.build()
-    n = 128
-    dims = (n, n, n)
-    pm = random_spheres(dims, count=48, rmin=4.0, rmax=10.0, seed=0)
-    st = torch.cuda.Stream()
-    R0 = 10.0 * (n ** 3) ** 0.5 * 5e-5
     dE1, dE2 = [0.0, 0.0, 5e-5, 0.0, 0.0, 0.0], [0.0, 0.0, 5e-6, 0.0, 0.0, 0.0]
-    out = {}
-    for name, h in (("secant", 0), ("consistent", 1)):
-        with torch.cuda.stream(st):
-            s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, stream=st, eta_eq=1e-6, eta_cg=1e-2,
-                          max_nr=2000, R0=R0, Rmax=R0, hessian=h)
-        first = s.solve_step(dE1, free_mask=FREE, raise_on_error=False)
-        ref = s.get_state()
-        eps0, kap0 = ref["eps"].clone(), ref["kappa"].clone()
+    st = torch.cuda.Stream()
+    sizes = {}
+    launches = 0
+    for n in [int(x) for x in args.onset_sizes.split(",")]:
+        dims = (n, n, n)
+        pm = random_spheres(dims, count=144 if n >= 256 else 48, rmin=4.0, rmax=10.0, seed=0)
+        R0 = 10.0 * (n ** 3) ** 0.5 * 5e-5
+        out, fields = {}, {}
+        for name, h in (("secant", 0), ("consistent", 1)):
+            with torch.cuda.stream(st):
+                s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, stream=st, eta_eq=1e-6, eta_cg=1e-2,
+                              max_nr=2000, R0=R0, Rmax=R0, hessian=h)
+            first = s.solve_step(dE1, free_mask=FREE, raise_on_error=False)
+            ref = s.get_state()
+            eps0, kap0 = ref["eps"].clone(), ref["kappa"].clone()
 
-        def step():
-            s.set_state(eps0, kap0)
-            return s.solve_step(dE2, free_mask=FREE, raise_on_error=False)
+            def step():
+                s.set_state(eps0, kap0)
+                return s.solve_step(dE2, free_mask=FREE, raise_on_error=False)
 
-        for _ in range(args.warmup):
-            step()
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        hv0, l0 = s.hv_count, s.launch_count
-        ev0.record(st)
-        reps = [step() for _ in range(args.steps)]
-        ev1.record(st)
-        torch.cuda.synchronize()
-        out[name] = {"ms": ev0.elapsed_time(ev1) / args.steps, "hv": (s.hv_count - hv0) / args.steps,
-                     "launches": s.launch_count - l0, "first_nr": first["nr_iters"],
-                     "nr_iters": [r["nr_iters"] for r in reps], "converged": [r["converged"] for r in reps],
-                     "mean_stress_zz": [r["mean_stress"][2] for r in reps],
-                     "damaged_voxels": int((s.get_state()["kappa"] > 1e-4).sum().item())}
-        s.close()
-    c, sc = out["consistent"], out["secant"]
+            for _ in range(args.warmup):
+                step()
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            hv0, l0 = s.hv_count, s.launch_count
+            ev0.record(st)
+            reps = [step() for _ in range(args.steps)]
+            ev1.record(st)
+            torch.cuda.synchronize()
+            launches += s.launch_count - l0
+            fin = s.get_state()
+            fields[name] = (fin["eps"].double().cpu(), fin["kappa"].double().cpu())
+            out[name] = {"ms": ev0.elapsed_time(ev1) / args.steps, "hv": (s.hv_count - hv0) / args.steps,
+                         "first_nr": first["nr_iters"], "first_converged": first["converged"],
+                         "nr_iters": [r["nr_iters"] for r in reps], "converged": [r["converged"] for r in reps],
+                         "rel_residual": [r["rel_residual"] for r in reps],
+                         "mean_stress": reps[-1]["mean_stress"],
+                         "damaged_voxels": int((s.get_state()["kappa"] > 1e-4).sum().item())}
+            s.close()
+        c, sc = out["consistent"], out["secant"]
+        ds = sum((a - b) ** 2 for a, b in zip(c["mean_stress"], sc["mean_stress"])) ** 0.5
+        ns = sum(b ** 2 for b in sc["mean_stress"]) ** 0.5
+        (ec, kc), (es, ks) = fields["consistent"], fields["secant"]
+        dc, dsec = kc > 1e-4, ks > 1e-4
+        near = (kc - 1e-4).abs() <= 1e-7
+        sizes[str(n)] = {"consistent": c, "secant": sc, "speedup_over_secant": sc["ms"] / c["ms"],
+                         "mean_stress_rel_diff": ds / ns if ns > 0 else None,
+                         "strain_field_rel_l2_diff": float((ec - es).norm() / es.norm()),
+                         "damaged_set_differences": int((dc != dsec).sum()),
+                         "damaged_set_differences_beyond_1e-3_of_kappa0": int(((dc != dsec) & ~near).sum()),
+                         "voxel_hv_per_s_consistent": c["hv"] * n ** 3 / (c["ms"] / 1e3)}
+    first = sizes[sorted(sizes, key=int)[0]]
     line = {
-        "metric": "load-step time at the damage onset, 128³: symmetric consistent vs secant Hessian",
-        "value": c["ms"], "unit": "ms/load step", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": c["ms"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": ONSET_WORKLOAD, "consistent": c, "secant": sc,
-                   "speedup_over_secant": sc["ms"] / c["ms"],
-                   "voxel_hv_per_s_consistent": c["hv"] * n ** 3 / (c["ms"] / 1e3)},
-        "gpu_launches": c["launches"],
+        "metric": "load-step time at the damage onset: symmetric consistent vs secant Hessian",
+        "value": first["consistent"]["ms"], "unit": "ms/load step (smallest size)", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": first["consistent"]["ms"],
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": ONSET_WORKLOAD, "sizes": sizes},
+        "gpu_launches": launches,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -918,6 +998,8 @@ def main():
         return run_hv(args)
     if args.workload == "lbfgs":
         return run_lbfgs(args)
+    if args.workload == "control":
+        return run_control(args)
     if args.workload == "onset":
         return run_onset(args)
     return run_gpu(args)

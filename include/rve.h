@@ -443,6 +443,13 @@ long long rve_launch_count(rve_t);
  * on (rve_pass_timing) the host steps the iterations and waits after each. */
 long long rve_sync_count(rve_t);
 
+/* Where the Steihaug-CG iterations are driven from, for benchmarks and
+ * tests (not part of the method): 1 (default) on the device, as the graph
+ * loop described at rve_sync_count; 0 from the host, one launch sequence
+ * and one wait per iteration.  Both run the same kernels in the same order
+ * and give identical results. */
+rve_status rve_set_device_loop(rve_t, int enable);
+
 /* Free the context and its workspaces.  NULL is ignored. */
 void rve_destroy(rve_t);
 

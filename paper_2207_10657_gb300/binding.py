@@ -126,6 +126,7 @@ _SIGS = [
     ("rve_hv_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("rve_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("rve_sync_count", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("rve_set_device_loop", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("rve_destroy", None, [ctypes.c_void_p]),
 ]
 
@@ -443,6 +444,10 @@ def rve_hv_count(h):
 
 def rve_sync_count(h):
     return lib().rve_sync_count(h)
+
+
+def rve_set_device_loop(h, enable=True):
+    check(lib().rve_set_device_loop(h, 1 if enable else 0), h)
 
 
 def rve_launch_count(h):

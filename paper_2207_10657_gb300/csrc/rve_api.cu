@@ -91,6 +91,7 @@ struct rve_ctx {
   CgGraph cg_graph[kCgGraphs];
   long long cg_graph_clock = 0;
   bool cg_graph_ok = true;     // false after a graph could not be built: host-driven loop
+  bool device_loop = true;     // rve_set_device_loop
   long long host_syncs = 0;    // stream synchronisations that read device scalars
   std::string err = "no error";
   long long hv = 0, launches = 0;
@@ -357,7 +358,7 @@ rve_status steihaug(rve_ctx* c, rve_step_report* rep) {
   if (s != RVE_OK) return s;
   if (c->Sh->status == CG_NONFINITE) return fail(c, RVE_ERR_NONFINITE, "non-finite gradient in CG");
   if (c->Sh->status != CG_RUN) return RVE_OK;
-  CgGraph* gr = (c->cg_graph_ok && !c->timer.on) ? cg_graph_for<R>(c) : nullptr;
+  CgGraph* gr = (c->device_loop && c->cg_graph_ok && !c->timer.on) ? cg_graph_for<R>(c) : nullptr;
   for (;;) {
     const int it0 = c->Sh->iters;
     if (gr) {
@@ -1042,6 +1043,13 @@ const char* rve_last_error(rve_t c) { return c ? c->err.c_str() : g_create_error
 long long rve_hv_count(rve_t c) { return c ? c->hv : 0; }
 long long rve_launch_count(rve_t c) { return c ? c->launches : 0; }
 long long rve_sync_count(rve_t c) { return c ? c->host_syncs : 0; }
+
+rve_status rve_set_device_loop(rve_t c, int enable) {
+  if (!c) return RVE_ERR_ARG;
+  if (enable != 0 && enable != 1) return fail(c, RVE_ERR_ARG, "enable must be 0 or 1");
+  c->device_loop = enable == 1;
+  return RVE_OK;
+}
 
 void rve_destroy(rve_t c) {
   if (!c) return;

@@ -61,6 +61,7 @@ class RVESolver:
         self._ids = ids
         self.phases = [p if isinstance(p, Phase) else Phase(*p) for p in phases]
         self.opts = make_opts(precision, **opts)
+        self._in()
         self.h = B.rve_create(self.dims, self.ndim, ids.data_ptr(), [p.as_tuple() for p in self.phases],
                               self.opts, self.stream.cuda_stream)
 
@@ -82,27 +83,49 @@ class RVESolver:
                              f"got {t.dtype} {tuple(t.shape)} on {t.device}")
         return t.data_ptr()
 
+    def _in(self):
+        """The library's stream waits for the work the caller's current
+        stream has queued (inputs written there)."""
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+
+    def _out(self):
+        """The caller's current stream waits for the library's stream
+        (outputs written there)."""
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
+
     # ------------------------------------------------------------ API
     def hessp(self, v, out=None):
         out = self.field() if out is None else out
+        self._in()
         B.rve_hessp(self.h, self._chk(v), self._chk(out))
+        self._out()
         return out
 
     def project(self, v, out=None):
         out = self.field() if out is None else out
+        self._in()
         B.rve_project(self.h, self._chk(v), self._chk(out))
+        self._out()
         return out
 
     def set_state(self, eps, kappa=None):
+        self._in()
         B.rve_set_state(self.h, self._chk(eps), self._chk(kappa, "scalar") if kappa is not None else 0)
 
     def get_state(self):
         eps, sig = self.field(), self.field()
         kap, dmg = self.scalar_field(), self.scalar_field()
+        self._in()
         B.rve_get_state(self.h, eps.data_ptr(), kap.data_ptr(), sig.data_ptr(), dmg.data_ptr())
+        self._out()
         return {"eps": eps, "sigma": sig, "kappa": kap, "damage": dmg}
 
     def set_damage(self, D):
+        self._in()
         B.rve_set_damage(self.h, self._chk(D, "scalar"))
 
     def set_free_mask(self, mask):
@@ -121,11 +144,14 @@ class RVESolver:
 
     def energy_grad(self, p=None, want_grad=True):
         grad = self.field() if want_grad else None
+        self._in()
         dW, dm = B.rve_energy_grad(self.h, self._chk(p) if p is not None else 0,
                                    grad.data_ptr() if grad is not None else 0)
+        self._out()
         return dW, dm, grad
 
     def solve_step(self, dE, free_mask=None, init=None, raise_on_error=True):
+        self._in()
         st, rep = B.rve_solve_step(self.h, dE, free_mask, self._chk(init) if init is not None else 0,
                                    raise_on_error)
         d = _report_dict(rep)
@@ -136,7 +162,9 @@ class RVESolver:
         """One Steihaug-CG solve (Algorithm 1) at the state with radius R:
         returns (z, report dict with the exit reason)."""
         out = self.field() if out is None else out
+        self._in()
         rep = B.rve_steihaug(self.h, R, eta_cg, self._chk(out))
+        self._out()
         return out, {"reason": B.CG_EXIT.get(rep.status, str(rep.status)), "iters": rep.iters,
                      "hv_products": rep.hv_products, "restarts": rep.restarts}
 
@@ -144,6 +172,7 @@ class RVESolver:
         """One load step by L-BFGS with the first-order incremental energy in
         its line search (report: nr_iters = iterations, cg_iters = line-search
         trials, rejected = step halvings, restarts = skipped pairs)."""
+        self._in()
         st, rep = B.rve_solve_step_lbfgs(self.h, dE, free_mask, memory, max_iter, raise_on_error)
         d = _report_dict(rep)
         d["status"] = st
@@ -200,8 +229,19 @@ class RVEBatch:
             self._ids.append(t)
         self.phases = [p if isinstance(p, Phase) else Phase(*p) for p in phases]
         self.opts = make_opts(32, **opts)
+        self._in()
         self.h = B.rve_batch_create(self.dims, [t.data_ptr() for t in self._ids],
                                     [p.as_tuple() for p in self.phases], self.opts, self.stream.cuda_stream)
+
+    def _in(self):
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+
+    def _out(self):
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
 
     def field(self, i):
         return torch.empty((self.ncomp[i],) + self.shapes[i], dtype=torch.float32, device=self.device)
@@ -211,17 +251,23 @@ class RVEBatch:
         for i, v in enumerate(vs):
             if v.dtype != torch.float32 or tuple(v.shape) != (self.ncomp[i],) + self.shapes[i] or not v.is_contiguous():
                 raise ValueError(f"member {i}: bad field")
+        self._in()
         B.rve_batch_hessp(self.h, [v.data_ptr() for v in vs], [o.data_ptr() for o in outs])
+        self._out()
         return outs
 
     def set_damage(self, i, D):
-        B.rve_batch_set_damage(self.h, i, D.contiguous().data_ptr())
+        D = D.contiguous()
+        self._in()
+        B.rve_batch_set_damage(self.h, i, D.data_ptr())
 
     def get_state(self, i):
         eps, sig = self.field(i), self.field(i)
         kap = torch.empty(self.shapes[i], dtype=torch.float32, device=self.device)
         dmg = torch.empty_like(kap)
+        self._in()
         B.rve_batch_get_state(self.h, i, eps.data_ptr(), kap.data_ptr(), sig.data_ptr(), dmg.data_ptr())
+        self._out()
         return {"eps": eps, "sigma": sig, "kappa": kap, "damage": dmg}
 
     def reset(self):

@@ -2,8 +2,8 @@
 node repeats Algorithm 1's iteration until an exit or a restart) and give
 the same load steps as the host-stepped loop (needs a GB300).
 
-The host-stepped loop is the one taken while per-pass timing is on
-(rve_pass_timing): both run the same kernels in the same order, so the
+The host-stepped loop is selected with rve_set_device_loop(h, 0): both run
+the same kernels in the same order, so the
 reports (Newton and CG iteration counts, restarts, rejections) must be
 identical and the stresses equal to the last bit in FP64 and to FP32
 rounding in FP32; the device loop must wait on the host far less (about
@@ -26,7 +26,7 @@ def _path(dims, pm, phases, incs, free, precision, host_stepped, **opts):
     build.build()
     s = RVESolver(dims, pm, phases, precision=precision, **opts)
     if host_stepped:
-        binding.rve_pass_timing(s.h, True)
+        binding.rve_set_device_loop(s.h, False)
     reps, s0 = [], s.sync_count
     for dE in incs:
         reps.append(s.solve_step(dE, free_mask=free, raise_on_error=False))

@@ -103,6 +103,8 @@ def _args():
     p.add_argument("--ws-train-seconds", type=float, default=120.0,
                    help="warmstart: time budget of the training-data generation (plain solves at 64^3)")
     p.add_argument("--ws-iters", type=int, default=4000, help="warmstart: Adam iterations")
+    p.add_argument("--ws-hessian", type=int, default=1, choices=[0, 1],
+                   help="warmstart: Hessian of every solve (0 secant, 1 symmetric consistent tangent)")
     p.add_argument("--ws-eval", default="128,128,192", help="warmstart: held-out evaluation grids")
     p.add_argument("--probe", choices=["step", "fno"], default=None,
                    help="untimed small case for profilers: 'step' = one load step of a 256x256x128 sphere cell, "
@@ -892,7 +894,7 @@ def run_warmstart(args):
     _build.build()
     phases = [MATRIX, STIFF]
     dE = [0.0, 0.0, 1e-5, 0.0, 0.0, 0.0]
-    opts = dict(eta_eq=1e-6, eta_cg=1e-2)
+    opts = dict(eta_eq=1e-6, eta_cg=1e-2, hessian=args.ws_hessian)
 
     def cell(n, seed):
         return random_spheres((n, n, n), count=48, rmin=4.0 * n / 128, rmax=10.0 * n / 128, seed=seed)
@@ -929,6 +931,7 @@ def run_warmstart(args):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32 solver / bf16 network",
         "data": "synthetic",
         "config": {"workload": WS_WORKLOAD, "eval_grids": args.ws_eval,
+                   "hessian": "symmetric consistent" if args.ws_hessian else "secant",
                    "train_samples": len(Xs), "train_generation_s": t_gen, "train_iters": args.ws_iters,
                    "train_s": t_train, "train_ms_per_iter": t_train / args.ws_iters * 1e3,
                    "loss_zero_prediction": zero, "loss_last_100": float(np.mean(hist[-100:])),

@@ -86,6 +86,7 @@ def _args():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n", type=int, default=N, help="grid size (default 256)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-onset", action="store_true", help="skip the damage-onset step of the default line")
     p.add_argument("--workload", default="rve256",
                    choices=["rve256", "asr", "lbfgs", "onset", "batch96", "warmstart", "hv", "control"],
                    help="rve256: the 256^3 sphere cell (default); asr: the same cell as an ASR-like "
@@ -257,6 +258,34 @@ def _oracle_hv_time(n, reps=1):
     return ts
 
 
+def _oracle_hv_worker(args):
+    """One spawned process: set up the oracle's product on an n^3 cell, wait
+    for the others, time one product."""
+    n, barrier = args
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    rve, D, v = _oracle_hv_setup(n)
+    barrier.wait()
+    t0 = time.perf_counter()
+    rve.hessp(D, v)
+    return time.perf_counter() - t0
+
+
+def _oracle_hv_all_cores(n):
+    """The oracle's product timed on every host core at once: one
+    single-threaded process per core (spawned: this process has a CUDA
+    context), each on its own copy of the n^3 cell.  Returns (voxel-Hv/s of
+    all processes together, processes, slowest time)."""
+    import multiprocessing as mp
+    procs = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        barrier = mgr.Barrier(procs)
+        with ctx.Pool(procs) as pool:
+            ts = pool.map(_oracle_hv_worker, [(n, barrier)] * procs)
+    return procs * n ** 3 / max(ts), procs, max(ts)
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -303,6 +332,7 @@ def _pass_bytes(n, pass_name):
         # CG products: the x-inverse applies z += alpha d, r += alpha Hd (reads z, r, d;
         # writes z, r) instead of storing Hd
         "x_inv": spec + 5 * field,
+        "x_inv_plain": spec + field,  # the product alone (rve_hessp): the half spectrum in, H v out
         "trial": nvox * (24 + 24 + 4 + 24 + 4 + 1 + 24 + 4 + 4),
         "cg_vec": nvox * 96,  # direction update: reads z, r, d, writes d
     }.get(pass_name)
@@ -443,6 +473,13 @@ def run_gpu(args):
     hv_bytes = sum(_pass_bytes(n, k) for k in hv_passes)
     nprod = max(stats["z_proj"][0], 1)
 
+    # ---------------- a load step at the damage onset (past kappa0), where the
+    # Newton iterations and not the product dominate: both Hessians
+    onset = None
+    if rank == 0 and not asr and not args.no_onset:
+        onset, _ = _onset_measure(n, 1, 1, st)
+        onset = {"workload": ONSET_WORKLOAD, **onset}
+
     if rank != 0:
         return 0
     cpu = None
@@ -452,9 +489,15 @@ def run_gpu(args):
             for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
                 os.environ.setdefault(var, "1")
             ts = _oracle_hv_time(n, reps=1)
-            cpu = {"value": nvox / ts[0], "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"one FP64 Hessian-vector product of the {n}^3 workload (damage snapshot "
-                             f"D~U[0,0.9]), numpy, 1 thread, {ts[0]:.1f} s"}
+            n_all = min(n, 128)
+            v_all, procs, t_all = _oracle_hv_all_cores(n_all)
+            cpu = {"value": v_all, "unit": UNIT, "cores": procs, "kind": "oracle",
+                   "sample": f"one FP64 Hessian-vector product in each of {procs} single-threaded processes at "
+                             f"once (one per host core), each on its own {n_all}^3 cell of the same sphere model "
+                             f"(damage snapshot D~U[0,0.9]), numpy; slowest process {t_all:.1f} s",
+                   "one_core": {"value": nvox / ts[0], "unit": UNIT, "cores": 1,
+                                "sample": f"one FP64 Hessian-vector product of the {n}^3 workload, numpy, "
+                                          f"1 thread, {ts[0]:.1f} s"}}
         except Exception as ex:  # report, do not hide
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
 
@@ -470,6 +513,7 @@ def run_gpu(args):
                    "converged": [r["converged"] for r in timed],
                    "mean_stress_zz": [r["mean_stress"][2] for r in timed],
                    "mean_strain_volumetric": [sum(r["mean_strain"][:3]) for r in timed],
+                   "onset_step": onset,
                    "host_waits_per_step": syncs / args.steps,
                    "host_stepped_cg": {"ms_per_step": ms_host / args.steps,
                                        "host_waits_per_step": syncs_host / args.steps},
@@ -480,9 +524,12 @@ def run_gpu(args):
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_launch},
         "hv_roofline": {"bound": "hbm", "passes": hv_passes,
+                        "what": "one CG iteration's product: the five passes with the Steihaug iterate / residual "
+                                "update fused into the x-inverse (its reads of z, r, d and writes of z, r counted)",
                         "achieved": hv_bytes / (hv_only_ms / nprod / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": hv_bytes / (hv_only_ms / nprod / 1e3) / 1e9 / peak,
-                        "algorithmic_bytes_per_product": hv_bytes},
+                        "algorithmic_bytes_per_product": hv_bytes,
+                        "product_alone_bytes": hv_bytes - _pass_bytes(n, "x_inv") + _pass_bytes(n, "x_inv_plain")},
         "compulsory_fraction": {"bytes_per_voxel": 53, "frac": 53 * nvox / (hv_only_ms / nprod / 1e3) / 1e9 / peak},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 6 * nvox * 4,
@@ -747,67 +794,76 @@ ONSET_WORKLOAD = ("random-sphere cells (48 spheres at 128^3, 144 at 256^3, r~U[4
                   "symmetric consistent tangent")
 
 
+def _onset_measure(n, steps, warmup, st):
+    """One load step at the damage onset of the n^3 sphere cell (48 spheres
+    at 128^3, 144 at 256^3), timed with the secant and with the symmetric
+    consistent Hessian from the same converged first increment."""
+    import torch
+    from paper_2207_10657_gb300 import RVESolver
+    from synth import random_spheres
+    dE1, dE2 = [0.0, 0.0, 5e-5, 0.0, 0.0, 0.0], [0.0, 0.0, 5e-6, 0.0, 0.0, 0.0]
+    dims = (n, n, n)
+    pm = random_spheres(dims, count=144 if n >= 256 else 48, rmin=4.0, rmax=10.0, seed=0)
+    R0 = 10.0 * (n ** 3) ** 0.5 * 5e-5
+    out, fields, launches = {}, {}, 0
+    for name, h in (("secant", 0), ("consistent", 1)):
+        with torch.cuda.stream(st):
+            s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, stream=st, eta_eq=1e-6, eta_cg=1e-2,
+                          max_nr=2000, R0=R0, Rmax=R0, hessian=h)
+        first = s.solve_step(dE1, free_mask=FREE, raise_on_error=False)
+        ref = s.get_state()
+        eps0, kap0 = ref["eps"].clone(), ref["kappa"].clone()
+
+        def step():
+            s.set_state(eps0, kap0)
+            return s.solve_step(dE2, free_mask=FREE, raise_on_error=False)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        hv0, l0 = s.hv_count, s.launch_count
+        ev0.record(st)
+        reps = [step() for _ in range(steps)]
+        ev1.record(st)
+        torch.cuda.synchronize()
+        launches += s.launch_count - l0
+        fin = s.get_state()
+        fields[name] = (fin["eps"].double().cpu(), fin["kappa"].double().cpu())
+        out[name] = {"ms": ev0.elapsed_time(ev1) / steps, "hv": (s.hv_count - hv0) / steps,
+                     "first_nr": first["nr_iters"], "first_converged": first["converged"],
+                     "nr_iters": [r["nr_iters"] for r in reps], "converged": [r["converged"] for r in reps],
+                     "rel_residual": [r["rel_residual"] for r in reps],
+                     "mean_stress": reps[-1]["mean_stress"],
+                     "damaged_voxels": int((fields[name][1] > 1e-4).sum().item())}
+        s.close()
+    c, sc = out["consistent"], out["secant"]
+    ds = sum((a - b) ** 2 for a, b in zip(c["mean_stress"], sc["mean_stress"])) ** 0.5
+    ns = sum(b ** 2 for b in sc["mean_stress"]) ** 0.5
+    (ec, kc), (es, ks) = fields["consistent"], fields["secant"]
+    dc, dsec = kc > 1e-4, ks > 1e-4
+    near = (kc - 1e-4).abs() <= 1e-7
+    return {"consistent": c, "secant": sc, "speedup_over_secant": sc["ms"] / c["ms"],
+            "mean_stress_rel_diff": ds / ns if ns > 0 else None,
+            "strain_field_rel_l2_diff": float((ec - es).norm() / es.norm()),
+            "damaged_set_differences": int((dc != dsec).sum()),
+            "damaged_set_differences_beyond_1e-3_of_kappa0": int(((dc != dsec) & ~near).sum()),
+            "voxel_hv_per_s_consistent": c["hv"] * n ** 3 / (c["ms"] / 1e3)}, launches
+
+
 def run_onset(args):
     """One load step at the damage onset with the secant and with the
     symmetric consistent Hessian (the converged state of a first increment
     is the reference state of every timed step), on the sphere cells of
     --onset-sizes (48 spheres at 128^3, 144 at 256^3, r ~ U[4, 10])."""
     import torch
-    from paper_2207_10657_gb300 import RVESolver, build as _build
-    from synth import random_spheres
+    from paper_2207_10657_gb300 import build as _build
     _build.build()
-    dE1, dE2 = [0.0, 0.0, 5e-5, 0.0, 0.0, 0.0], [0.0, 0.0, 5e-6, 0.0, 0.0, 0.0]
     st = torch.cuda.Stream()
-    sizes = {}
-    launches = 0
+    sizes, launches = {}, 0
     for n in [int(x) for x in args.onset_sizes.split(",")]:
-        dims = (n, n, n)
-        pm = random_spheres(dims, count=144 if n >= 256 else 48, rmin=4.0, rmax=10.0, seed=0)
-        R0 = 10.0 * (n ** 3) ** 0.5 * 5e-5
-        out, fields = {}, {}
-        for name, h in (("secant", 0), ("consistent", 1)):
-            with torch.cuda.stream(st):
-                s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, stream=st, eta_eq=1e-6, eta_cg=1e-2,
-                              max_nr=2000, R0=R0, Rmax=R0, hessian=h)
-            first = s.solve_step(dE1, free_mask=FREE, raise_on_error=False)
-            ref = s.get_state()
-            eps0, kap0 = ref["eps"].clone(), ref["kappa"].clone()
-
-            def step():
-                s.set_state(eps0, kap0)
-                return s.solve_step(dE2, free_mask=FREE, raise_on_error=False)
-
-            for _ in range(args.warmup):
-                step()
-            torch.cuda.synchronize()
-            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            hv0, l0 = s.hv_count, s.launch_count
-            ev0.record(st)
-            reps = [step() for _ in range(args.steps)]
-            ev1.record(st)
-            torch.cuda.synchronize()
-            launches += s.launch_count - l0
-            fin = s.get_state()
-            fields[name] = (fin["eps"].double().cpu(), fin["kappa"].double().cpu())
-            out[name] = {"ms": ev0.elapsed_time(ev1) / args.steps, "hv": (s.hv_count - hv0) / args.steps,
-                         "first_nr": first["nr_iters"], "first_converged": first["converged"],
-                         "nr_iters": [r["nr_iters"] for r in reps], "converged": [r["converged"] for r in reps],
-                         "rel_residual": [r["rel_residual"] for r in reps],
-                         "mean_stress": reps[-1]["mean_stress"],
-                         "damaged_voxels": int((s.get_state()["kappa"] > 1e-4).sum().item())}
-            s.close()
-        c, sc = out["consistent"], out["secant"]
-        ds = sum((a - b) ** 2 for a, b in zip(c["mean_stress"], sc["mean_stress"])) ** 0.5
-        ns = sum(b ** 2 for b in sc["mean_stress"]) ** 0.5
-        (ec, kc), (es, ks) = fields["consistent"], fields["secant"]
-        dc, dsec = kc > 1e-4, ks > 1e-4
-        near = (kc - 1e-4).abs() <= 1e-7
-        sizes[str(n)] = {"consistent": c, "secant": sc, "speedup_over_secant": sc["ms"] / c["ms"],
-                         "mean_stress_rel_diff": ds / ns if ns > 0 else None,
-                         "strain_field_rel_l2_diff": float((ec - es).norm() / es.norm()),
-                         "damaged_set_differences": int((dc != dsec).sum()),
-                         "damaged_set_differences_beyond_1e-3_of_kappa0": int(((dc != dsec) & ~near).sum()),
-                         "voxel_hv_per_s_consistent": c["hv"] * n ** 3 / (c["ms"] / 1e3)}
+        sizes[str(n)], nl = _onset_measure(n, args.steps, args.warmup, st)
+        launches += nl
     first = sizes[sorted(sizes, key=int)[0]]
     line = {
         "metric": "load-step time at the damage onset: symmetric consistent vs secant Hessian",

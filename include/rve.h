@@ -21,7 +21,10 @@
  *  - Fields are structure-of-arrays, component-major: element (c, z, y, x)
  *    at offset ((c*Nz + z)*Ny + y)*Nx + x, x fastest.  Components are
  *    Mandel-orthonormal: 3D (11, 22, 33, sqrt2*23, sqrt2*13, sqrt2*12),
- *    2D plane strain (11, 22, sqrt2*12).  ncomp = 6 (3D) or 3 (2D).
+ *    2D plane strain (11, 22, sqrt2*12).  ncomp = 6 (3D) or 3 (2D).  With
+ *    the triangle element (rve_solver_opts.element = 1) a field has two
+ *    strain points per pixel: ncomp x 2 x Nvox, element (c, q, y, x) at
+ *    ((c*2 + q)*Ny + y)*Nx + x, and per-point scalar fields 2 x Nvox.
  *  - Real type: float when the context was created with precision 32,
  *    double with precision 64.  Pointers named *_dev are DEVICE pointers,
  *    owned by the caller, 16-byte aligned, read/written on the context's
@@ -100,6 +103,18 @@ typedef struct {
                          generic path (d.Hd from the stored product, separate
                          update kernels).  FP64 fields and other lengths
                          always use the generic passes. */
+  int element;        /* finite-element gradient the projection is built from
+                         (Sec. 2.1, Eq. (9)): 0: one bilinear / trilinear
+                         element per voxel, one quadrature point (default);
+                         1: linear triangles, every pixel split along its main
+                         diagonal into the two triangles of axis order (x, y)
+                         and (y, x), one quadrature point each -- 2D only,
+                         secant Hessian only.  With 1 every strain-sized
+                         field holds ncomp x 2 x Nvox reals, layout
+                         [c][q][y][x] (triangle q = 0 for (x, y), 1 for
+                         (y, x)), and every per-point scalar field (history,
+                         damage) 2 x Nvox; the mean strain and stress average
+                         over all triangles. */
 } rve_solver_opts;
 
 /* Per-load-step statistics. */
@@ -125,7 +140,7 @@ typedef struct {
 /* Fill opts with defaults: eta_eq 1e-6, eta_nr 0, eta_cg 1e-2, eta_up 0.1,
  * R0 = Rmax = 0 (meaning "10 sqrt(Nvox) |dE|" at the first load step),
  * max_nr 50, max_cg 1000, restart_thr 0.2, precision 32, hessian 0,
- * passes 0. */
+ * passes 0, element 0. */
 void rve_default_opts(rve_solver_opts* opts);
 
 /* Create a context.  Sec. 2 (cell, strain split), Appendix A (phases).

@@ -24,7 +24,8 @@ class rve_solver_opts(ctypes.Structure):
     _fields_ = [("eta_eq", ctypes.c_double), ("eta_nr", ctypes.c_double), ("eta_cg", ctypes.c_double),
                 ("eta_up", ctypes.c_double), ("R0", ctypes.c_double), ("Rmax", ctypes.c_double),
                 ("max_nr", ctypes.c_int), ("max_cg", ctypes.c_int), ("restart_thr", ctypes.c_double),
-                ("precision", ctypes.c_int), ("hessian", ctypes.c_int), ("passes", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("hessian", ctypes.c_int), ("passes", ctypes.c_int),
+                ("element", ctypes.c_int)]
 
 
 class rve_step_report(ctypes.Structure):

@@ -132,13 +132,19 @@ __global__ void __launch_bounds__(zthreads<N>(), zminblocks<N>())
 }
 
 // ------------------------------------------------- y + projection (2D)
-template <int N>
+// NCL = 3: one element per pixel (Mandel components); NCL = 6: the two Kuhn
+// triangles of every pixel (lines c * 2 + q).
+template <int N, int NCL> constexpr int p2tx_l() {
+  return (kFBudget / (NCL * N)) < 16 ? ((kFBudget / (NCL * N)) < 1 ? 1 : kFBudget / (NCL * N)) : 16;
+}
+
+template <int N, int NCL>
 __global__ void __launch_bounds__(kFT)
     kf_yproj2d(float2* __restrict__ spec, const int nxh, const float2* __restrict__ tw,
                const float2* __restrict__ gdx, const float2* __restrict__ gax, const float2* __restrict__ gdy,
                const float2* __restrict__ gay, const unsigned free_mask) {
-  constexpr int TX = p2tx<N>();
-  constexpr int NL = 3 * TX;
+  constexpr int TX = p2tx_l<N, NCL>();
+  constexpr int NL = NCL * TX;
   __shared__ __align__(16) float2 buf[N * NL];
   const int kx0 = blockIdx.x * TX;
   const int tv = min(TX, nxh - kx0);
@@ -153,12 +159,18 @@ __global__ void __launch_bounds__(kFT)
     const int y = pt / TX, t = pt - (pt / TX) * TX;
     const int kx = kx0 + t;
     if (t >= tv) continue;
-    float2 m[3];
+    float2 m[NCL];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) m[c] = buf[y * NL + c * TX + t];
-    project2<float>(m, cmul(gdx[kx], gay[y]), cmul(gax[kx], gdy[y]), kx == 0 && y == 0, free_mask);
+    for (int c = 0; c < NCL; ++c) m[c] = buf[y * NL + c * TX + t];
+    if constexpr (NCL == 3) {
+      project2<float>(m, cmul(gdx[kx], gay[y]), cmul(gax[kx], gdy[y]), kx == 0 && y == 0, free_mask);
+    } else {
+      const float2 dx = gdx[kx], dy = gdy[y];
+      project_simplex2<float>(m, make_float2(1.f + dx.x, dx.y), dx, make_float2(1.f + dy.x, dy.y), dy,
+                              kx == 0 && y == 0, free_mask);
+    }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) buf[y * NL + c * TX + t] = m[c];
+    for (int c = 0; c < NCL; ++c) buf[y * NL + c * TX + t] = m[c];
   }
   __syncthreads();
   fft_ct<N, NL, kFT, true>(buf, tw);
@@ -189,7 +201,9 @@ static cudaError_t xfwd_n(const GridDesc& g, const float* in, const uint8_t* pha
     constexpr int Q = xq<N, 6>();
     const int blocks = (int)((g.nrows + Q - 1) / Q);
     *nblocks = blocks;
-    if (cons)
+    if (tangent && g.nq == 2)
+      kf_xfwd<N, 6, 3><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw, pd);
+    else if (cons)
       kf_xfwd<N, 6, 2><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw, pd, ct->dp, ct->a,
                                                 ct->n);
     else if (tangent) kf_xfwd<N, 6, 1><<<blocks, kFT, 0, st>>>(in, phase, dmg, mt, spec, g.nrows, g.nvox, tw, pd);
@@ -259,10 +273,15 @@ static cudaError_t zproj_n(const GridDesc& g, float2* spec, const SpecWork<float
 
 template <int N>
 static cudaError_t yproj2d_n(const GridDesc& g, float2* spec, const SpecWork<float>& w, cudaStream_t st) {
-  constexpr int TX = p2tx<N>();
-  const dim3 grid((g.nxh + TX - 1) / TX);
-  kf_yproj2d<N><<<grid, kFT, 0, st>>>(spec, g.nxh, w.tw[1], w.gdiff[0], w.gavg[0], w.gdiff[1], w.gavg[1],
-                                       w.free_mask);
+  if (g.ncomp == 6) {
+    constexpr int TX = p2tx_l<N, 6>();
+    kf_yproj2d<N, 6><<<(g.nxh + TX - 1) / TX, kFT, 0, st>>>(spec, g.nxh, w.tw[1], w.gdiff[0], w.gavg[0],
+                                                             w.gdiff[1], w.gavg[1], w.free_mask);
+  } else {
+    constexpr int TX = p2tx_l<N, 3>();
+    kf_yproj2d<N, 3><<<(g.nxh + TX - 1) / TX, kFT, 0, st>>>(spec, g.nxh, w.tw[1], w.gdiff[0], w.gavg[0],
+                                                             w.gdiff[1], w.gavg[1], w.free_mask);
+  }
   return cudaGetLastError();
 }
 

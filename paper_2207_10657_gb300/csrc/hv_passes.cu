@@ -111,7 +111,7 @@ cudaError_t spectral_setup(const GridDesc& g, SpecWork<R>& w) {
     w.tz = std::max(1, std::min(pow2_floor(std::max(1, ez / (6 * g.nz))), 16));
   } else {
     const int e2 = std::min(kYThreads * kYEpt, (int)(kSmemCap / sizeof(C)));
-    w.tz = std::max(1, std::min(pow2_floor(std::max(1, e2 / (3 * g.ny))), 64));
+    w.tz = std::max(1, std::min(pow2_floor(std::max(1, e2 / (g.ncomp * g.ny))), 64));
   }
   // up to three partial sums per x block (the fused CG x-inverse), and the
   // compile-time x passes may take a single row per block (Nx = 512)
@@ -149,7 +149,7 @@ cudaError_t spectral_plan(const GridDesc& g, SpecWork<R>& w) {
     w.tz = std::max(1, std::min(pow2_floor(std::max(1, ez / (6 * g.nz))), 16));
   } else {
     const int e2 = std::min(kYThreads * kYEpt, (int)(kSmemCap / sizeof(C)));
-    w.tz = std::max(1, std::min(pow2_floor(std::max(1, e2 / (3 * g.ny))), 64));
+    w.tz = std::max(1, std::min(pow2_floor(std::max(1, e2 / (g.ncomp * g.ny))), 64));
   }
   cudaFuncSetAttribute(k_xfwd<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
   cudaFuncSetAttribute(k_ycols<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap);
@@ -213,7 +213,7 @@ static cudaError_t spectral_middle(const GridDesc& g, SpecWork<R>& w, cudaStream
     }
     if (e == cudaErrorNotSupported) {
       const dim3 pg((g.nxh + w.tz - 1) / w.tz);
-      const size_t psm = (size_t)3 * w.tz * g.ny * sizeof(C);
+      const size_t psm = (size_t)g.ncomp * w.tz * g.ny * sizeof(C);
       k_yproj2d<R><<<pg, kYThreads, psm, st>>>(w.spec, g, w.tz, w.py, w.tw[1], w.gdiff[0], w.gavg[0], w.gdiff[1],
                                                w.gavg[1], w.free_mask);
       e = cudaGetLastError();

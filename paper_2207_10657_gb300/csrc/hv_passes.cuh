@@ -13,6 +13,8 @@ struct GridDesc {
   int ncomp;      // 3 or 6
   long long nvox;
   long long nrows;  // ny * nz voxel rows along x
+  int nq = 1;       // strain points per voxel: 1 (one element per voxel) or 2 (2D Kuhn
+                    // triangles; the spectral lines are then c * 2 + q, ncomp = 6)
 };
 
 // Rank-one part of the symmetric consistent damage tangent, per voxel: the

@@ -26,13 +26,14 @@ template <int N> constexpr int ytx() { return (kFBudget / N) < 16 ? (kFBudget / 
 template <int N> constexpr int ztx() { return N <= 64 ? 16 : 4; }
 template <int N> constexpr int zthreads() { return N >= 512 ? 512 : 256; }
 template <int N> constexpr int zminblocks() { return N >= 512 ? 1 : 3; }
-template <int N> constexpr int p2tx() { return (kFBudget / (3 * N)) < 16 ? (kFBudget / (3 * N)) : 16; }
 
 // ------------------------------------------------------------ x forward
 // One x-forward tile: the voxel rows [row0, row_end) (at most xq rows),
 // tangent applied on load, forward FFT of the real rows packed in pairs,
 // half spectrum stored.  Returns this thread's share of in : (tangent : in)
-// (MODE >= 1).  `buf` holds NC * xq / 2 lines of N.
+// (MODE >= 1).  `buf` holds NC * xq / 2 lines of N.  MODE 0: plain; 1:
+// secant tangent; 2: symmetric consistent tangent; 3: secant tangent of
+// the 2D Kuhn triangles (NC = 6 lines c * 2 + q).
 template <int N, int NC, int MODE>
 __device__ __forceinline__ float xfwd_rows(float2* buf, const float* __restrict__ in,
                                            const uint8_t* __restrict__ phase, const float* __restrict__ dmg,
@@ -61,7 +62,26 @@ __device__ __forceinline__ float xfwd_rows(float2* buf, const float* __restrict_
       const long long vox = row * N + x;
 #pragma unroll
       for (int c = 0; c < NC; ++c) v[b][c] = ok ? __ldg(in + c * nvox + vox) : 0.f;
-      if (MODE >= 1 && ok) {
+      if (MODE == 3 && ok) {
+        // 2D Kuhn triangles: line c * 2 + q is Mandel component c of
+        // triangle q, whose damage is dmg[q * nvox + vox]
+        const int ph = __ldg(phase + vox);
+        float dv = 0.f;
+#pragma unroll
+        for (int q2 = 0; q2 < 2; ++q2) {
+          const float keep = 1.f - __ldg(dmg + q2 * nvox + vox);
+          const float lam = mt.lam[ph] * keep, tmu = 2.f * mt.mu[ph] * keep;
+          const float tr = v[b][q2] + v[b][2 + q2];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float sg = tmu * v[b][2 * c + q2] + (c < 2 ? lam * tr : 0.f);
+            dv += v[b][2 * c + q2] * sg;
+            v[b][2 * c + q2] = sg;
+          }
+        }
+        acc += dv;
+      }
+      if ((MODE == 1 || MODE == 2) && ok) {
         const float keep = 1.f - __ldg(dmg + vox);
         const int ph = __ldg(phase + vox);
         const float lam = mt.lam[ph] * keep, tmu = 2.f * mt.mu[ph] * keep;

@@ -39,7 +39,17 @@ __device__ __forceinline__ void xfwd_body(const R* __restrict__ in, const uint8_
     if (row < g.nrows) {
       const long long vox = row * nx + x;
       for (int c = 0; c < nc; ++c) val[c] = in[c * g.nvox + vox];
-      if (MODE == 1) {
+      if (MODE == 1 && g.nq == 2) {
+        // 2D Kuhn triangles: line c * 2 + q is Mandel component c of triangle
+        // q, whose damage is dmg[q * nvox + vox]
+        const int ph = phase[vox];
+        for (int q2 = 0; q2 < 2; ++q2) {
+          const R keep = (R)1 - dmg[q2 * g.nvox + vox];
+          const R lam = mt.lam[ph] * keep, two_mu = (R)2 * mt.mu[ph] * keep;
+          const R tr = val[q2] + val[2 + q2];
+          for (int c = 0; c < 3; ++c) val[2 * c + q2] = two_mu * val[2 * c + q2] + (c < 2 ? lam * tr : (R)0);
+        }
+      } else if (MODE == 1) {
         const int ph = phase[vox];
         const R keep = (R)1 - dmg[vox];
         const R lam = mt.lam[ph] * keep, two_mu = (R)2 * mt.mu[ph] * keep;
@@ -190,22 +200,32 @@ __device__ __forceinline__ void yproj2d_body(Cx<R>* __restrict__ spec, const Gri
   using C = Cx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int ny = g.ny, nxh = g.nxh;
+  const int ny = g.ny, nxh = g.nxh, ncl = g.ncomp;  // lines per column: 3, or 6 for Kuhn triangles
   const int kx0 = bx * TX;
   const int tv = min(TX, nxh - kx0);
   const int plane = ny * TX;
-  for (int idx = threadIdx.x; idx < 3 * plane; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < ncl * plane; idx += blockDim.x) {
     const int c = idx / plane, rem = idx - c * plane;
     const int y = rem / TX, t = rem - y * TX;
     buf[idx] = t < tv ? spec[((long long)c * ny + y) * nxh + kx0 + t] : C{0, 0};
   }
   __syncthreads();
   const LineMap lm{TX, plane, 1, TX};
-  fft_lines<kYEpt, false, true>(buf, py, 3 * TX, lm, tw);
+  fft_lines<kYEpt, false, true>(buf, py, ncl * TX, lm, tw);
   for (int pt = threadIdx.x; pt < plane; pt += blockDim.x) {
     const int y = pt / TX, t = pt - y * TX;
     const int kx = kx0 + t;
     if (t >= tv) continue;
+    if (ncl == 6) {
+      C m[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) m[c] = buf[c * plane + pt];
+      const C dx = gdx[kx], dy = gdy[y];
+      project_simplex2<R>(m, C{(R)1 + dx.x, dx.y}, dx, C{(R)1 + dy.x, dy.y}, dy, kx == 0 && y == 0, free_mask);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) buf[c * plane + pt] = m[c];
+      continue;
+    }
     C m[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) m[c] = buf[c * plane + pt];
@@ -216,8 +236,8 @@ __device__ __forceinline__ void yproj2d_body(Cx<R>* __restrict__ spec, const Gri
     for (int c = 0; c < 3; ++c) buf[c * plane + pt] = m[c];
   }
   __syncthreads();
-  fft_lines<kYEpt, true, true>(buf, py, 3 * TX, lm, tw);
-  for (int idx = threadIdx.x; idx < 3 * plane; idx += blockDim.x) {
+  fft_lines<kYEpt, true, true>(buf, py, ncl * TX, lm, tw);
+  for (int idx = threadIdx.x; idx < ncl * plane; idx += blockDim.x) {
     const int c = idx / plane, rem = idx - c * plane;
     const int y = rem / TX, t = rem - y * TX;
     if (t < tv) spec[((long long)c * ny + y) * nxh + kx0 + t] = buf[idx];

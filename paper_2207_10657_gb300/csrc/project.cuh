@@ -75,4 +75,58 @@ __device__ __forceinline__ void project2(Cx<R> (&m)[3], Cx<R> d0, Cx<R> d1, bool
   m[2] = cscale(o(n0, n1, v0, v1), s2);
 }
 
+// Ghat(k) for the 2D Kuhn-triangle discretisation (every pixel split along
+// its main diagonal into two linear triangles, one strain each; Sec. 2.1
+// builds the projection from any FE gradient).  m holds the six lines
+// c * 2 + q: Mandel component c (11, 22, sqrt2*12) of triangle q.  The
+// triangle of axis order (x, y) has derivative symbols Dx0 = e^{i thx} - 1,
+// Dy0 = e^{i thx} (e^{i thy} - 1); the one of order (y, x) has
+// Dy1 = e^{i thy} - 1, Dx1 = e^{i thy} (e^{i thx} - 1).  The compatible
+// strains are B a (a in C^2, B stacking sym(Dq (x) a) over q) and the
+// orthogonal projector is B (B^H B)^-1 B^H: b = B^H m, a = M^-1 b with the
+// 2 x 2 Hermitian M = B^H B (non-singular for k != 0: linear triangles have
+// no zero-energy modes), m = B a.  At k = 0 a compatible field has the same
+// mean strain on both triangles: the free components keep the triangle
+// average, the strain-controlled ones vanish.  ex, ey: e^{i th}; dx, dy:
+// e^{i th} - 1 (exact zero at k = 0).
+template <typename R>
+__device__ __forceinline__ void project_simplex2(Cx<R> (&m)[6], Cx<R> ex, Cx<R> dx, Cx<R> ey, Cx<R> dy, bool k0,
+                                                 unsigned free_mask) {
+  using C = Cx<R>;
+  if (k0) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const C avg = ((free_mask >> c) & 1u) ? cscale(cadd(m[2 * c], m[2 * c + 1]), (R)0.5) : C{0, 0};
+      m[2 * c] = avg;
+      m[2 * c + 1] = avg;
+    }
+    return;
+  }
+  const R is2 = (R)0.70710678118654752440;
+  const C Dx[2] = {dx, cmul(ey, dx)}, Dy[2] = {cmul(ex, dy), dy};
+  C bx{0, 0}, by{0, 0}, mxy{0, 0};
+  R mxx = 0, myy = 0;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const R ax = Dx[q].x * Dx[q].x + Dx[q].y * Dx[q].y, ay = Dy[q].x * Dy[q].x + Dy[q].y * Dy[q].y;
+    mxx += ax + (R)0.5 * ay;
+    myy += ay + (R)0.5 * ax;
+    mxy = cadd(mxy, cscale(cmulc(Dx[q], Dy[q]), (R)0.5));  // conj(Dy) Dx / 2
+    const C s12 = cscale(m[4 + q], is2);
+    bx = cadd(bx, cadd(cmulc(m[q], Dx[q]), cmulc(s12, Dy[q])));
+    by = cadd(by, cadd(cmulc(m[2 + q], Dy[q]), cmulc(s12, Dx[q])));
+  }
+  const R det = mxx * myy - (mxy.x * mxy.x + mxy.y * mxy.y);
+  const R inv = (R)1 / det;
+  // a = M^-1 b with M = [[mxx, mxy], [conj(mxy), myy]]
+  const C ax = cscale(csub(cscale(bx, myy), cmul(mxy, by)), inv);
+  const C ay = cscale(csub(cscale(by, mxx), cmulc(bx, mxy)), inv);
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    m[q] = cmul(Dx[q], ax);
+    m[2 + q] = cmul(Dy[q], ay);
+    m[4 + q] = cscale(cadd(cmul(Dy[q], ax), cmul(Dx[q], ay)), is2);
+  }
+}
+
 }  // namespace rve

@@ -85,7 +85,8 @@ constexpr int kCgGraphs = 4;
 
 struct rve_ctx {
   int precision = 32;
-  GridDesc g{};
+  GridDesc g{};   // strain points (voxels, or the triangles of every pixel): the pointwise kernels
+  GridDesc gs{};  // the spectral passes (voxels, with nq lines per Mandel component)
   cudaStream_t st = nullptr;
   cudaStream_t cap = nullptr;  // private stream the Steihaug graphs are captured on
   CgGraph cg_graph[kCgGraphs];
@@ -183,7 +184,7 @@ rve_status create_impl(rve_ctx* c, const uint8_t* phase_ids, const rve_phase* ph
     m->mt.kappa0[i] = (R)phases[i].kappa0;
     m->mt.kappaf[i] = (R)phases[i].kappaf;
   }
-  CK(spectral_setup<R>(g, m->sw), "spectral setup");
+  CK(spectral_setup<R>(c->gs, m->sw), "spectral setup");
   m->sw.timer = &c->timer;
   m->sw.generic = c->opts.passes == 1;
   m->sw.unfused = c->opts.passes == 2;
@@ -199,15 +200,19 @@ rve_status create_impl(rve_ctx* c, const uint8_t* phase_ids, const rve_phase* ph
     CK(cudaMalloc(&m->cn, nf), "consistent-tangent allocation");
     m->sw.cons = ConsTan<R>{m->cdp, m->ca, m->cn};
   }
+  // one phase id per strain point: the voxel's id, repeated for each of its
+  // triangles (point q * Nvox + v)
+  const long long nv = c->gs.nvox;
   CK(cudaMalloc(&m->phase, g.nvox), "phase allocation");
   CK(cudaMalloc(&m->S, sizeof(DevScalars)), "scalar allocation");
   CK(cudaMemsetAsync(m->S, 0, sizeof(DevScalars), c->st), "memset");
-  CK(cudaMemcpyAsync(m->phase, phase_ids, g.nvox, cudaMemcpyDeviceToDevice, c->st), "phase copy");
+  for (int q = 0; q < c->gs.nq; ++q)
+    CK(cudaMemcpyAsync(m->phase + q * nv, phase_ids, nv, cudaMemcpyDeviceToDevice, c->st), "phase copy");
   // validate ids once
-  std::vector<uint8_t> ids(g.nvox);
-  CK(cudaMemcpyAsync(ids.data(), m->phase, g.nvox, cudaMemcpyDeviceToHost, c->st), "phase check copy");
+  std::vector<uint8_t> ids(nv);
+  CK(cudaMemcpyAsync(ids.data(), m->phase, nv, cudaMemcpyDeviceToHost, c->st), "phase check copy");
   CK(cudaStreamSynchronize(c->st), "synchronize");
-  for (long long i = 0; i < g.nvox; ++i)
+  for (long long i = 0; i < nv; ++i)
     if (ids[i] >= nphase) return fail(c, RVE_ERR_ARG, "phase id out of range at voxel " + std::to_string(i));
   CK(cudaMemsetAsync(m->eps, 0, nf, c->st), "memset");
   CK(cudaMemsetAsync(m->khist, 0, ns, c->st), "memset");
@@ -244,11 +249,11 @@ cudaError_t issue_cg_iteration(rve_ctx* c, cudaStream_t st, long long* nl) {
   cudaError_t e = cudaErrorNotSupported;
   if constexpr (std::is_same<R, float>::value) {
     AlphaArg aa{m->S, st, nl};
-    e = spectral_hv_cg(g, m->sw, m->mt, m->d, m->phase, m->D, m->z, m->r, &m->S->dHd, launch_alpha, &aa,
+    e = spectral_hv_cg(c->gs, m->sw, m->mt, m->d, m->phase, m->D, m->z, m->r, &m->S->dHd, launch_alpha, &aa,
                        &m->S->status, &m->S->alpha, &m->S->tau, &m->S->rr_new, st, nl);
   }
   if (e == cudaErrorNotSupported) {
-    e = spectral_apply<R>(g, m->sw, m->mt, m->d, m->phase, m->D, XIn::Tangent, m->Hd, m->d, &m->S->dHd, st, nl);
+    e = spectral_apply<R>(c->gs, m->sw, m->mt, m->d, m->phase, m->D, XIn::Tangent, m->Hd, m->d, &m->S->dHd, st, nl);
     if (e == cudaSuccess) e = cg_alpha(m->S, st, nl);
     if (e == cudaSuccess) {
       PassScope ps(&c->timer, st, PASS_CGVEC);
@@ -374,7 +379,8 @@ rve_status steihaug(rve_ctx* c, rve_step_report* rep) {
     if (c->Sh->status != CG_RUN) break;
     if (c->Sh->restart) {
       // Eq. (20): r = H z + g, beta = 0, then the direction
-      CK(spectral_apply<R>(g, m->sw, m->mt, m->z, m->phase, m->D, XIn::Tangent, m->tmp, nullptr, nullptr, c->st, nl),
+      CK(spectral_apply<R>(c->gs, m->sw, m->mt, m->z, m->phase, m->D, XIn::Tangent, m->tmp, nullptr, nullptr, c->st,
+                           nl),
          "hessp (restart)");
       ++c->hv;
       if (rep) ++rep->hv_products;
@@ -395,7 +401,7 @@ rve_status steihaug(rve_ctx* c, rve_step_report* rep) {
 template <typename R>
 rve_status gradient(rve_ctx* c) {
   Impl<R>* m = impl_of<R>(c);
-  CK(spectral_apply<R>(c->g, m->sw, m->mt, m->sig, m->phase, m->D, XIn::Plain, m->g, m->g, &m->S->gg, c->st,
+  CK(spectral_apply<R>(c->gs, m->sw, m->mt, m->sig, m->phase, m->D, XIn::Plain, m->g, m->g, &m->S->gg, c->st,
                        &c->launches),
      "gradient");
   return RVE_OK;
@@ -420,7 +426,7 @@ rve_status solve_step_impl(rve_ctx* c, const double dE[6], const void* init, rve
   }
   CK(add_uniform<R>(g, m->eps, dE, c->st, nl), "load increment");
   if (init) {
-    CK(spectral_apply<R>(g, m->sw, m->mt, (const R*)init, m->phase, m->D, XIn::Plain, m->tmp, nullptr, nullptr,
+    CK(spectral_apply<R>(c->gs, m->sw, m->mt, (const R*)init, m->phase, m->D, XIn::Plain, m->tmp, nullptr, nullptr,
                          c->st, nl),
        "warm start projection");
     CK(axpy<R>((long long)g.ncomp * g.nvox, (R)1, m->tmp, m->eps, c->st, nl), "warm start add");
@@ -614,7 +620,7 @@ rve_status lbfgs_step_impl(rve_ctx* c, const double dE[6], int mem, int max_iter
     std::swap(m->sig, m->sig_t);
     std::swap(m->D, m->D_t);
     std::swap(m->kap, m->kap_t);
-    CK(spectral_apply<R>(g, m->sw, m->mt, m->sig, m->phase, m->D, XIn::Plain, m->r, m->r, &m->S->gg, c->st, nl),
+    CK(spectral_apply<R>(c->gs, m->sw, m->mt, m->sig, m->phase, m->D, XIn::Plain, m->r, m->r, &m->S->gg, c->st, nl),
        "gradient");
     CK(lb_pair<R>(n, m->d, m->g, m->r, m->L, part, c->st, nl), "pair update");
     CK(cudaMemcpyAsync(m->Lh, m->L, sizeof(LbScalars), cudaMemcpyDeviceToHost, c->st), "read L-BFGS scalars");
@@ -697,7 +703,7 @@ rve_status stiffness_impl(rve_ctx* c, double tol, int max_cg, double* Cbar, int*
     cudaError_t ce = cudaMemsetAsync(m->tmp, 0, (size_t)g.ncomp * g.nvox * sizeof(R), c->st);
     if (ce == cudaSuccess) ce = add_uniform<R>(g, m->tmp, e, c->st, nl);
     if (ce == cudaSuccess)
-      ce = spectral_apply<R>(g, m->sw, m->mt, m->tmp, m->phase, m->D, XIn::Tangent, m->g, m->g, &m->S->gg, c->st,
+      ce = spectral_apply<R>(c->gs, m->sw, m->mt, m->tmp, m->phase, m->D, XIn::Tangent, m->g, m->g, &m->S->gg, c->st,
                              nl);
     if (ce != cudaSuccess) {
       s = cuda_fail(c, ce, "stiffness right-hand side");
@@ -784,7 +790,7 @@ rve_status energy_grad_impl(rve_ctx* c, const void* p, double* dW, double* dm, v
   k_energy_s<<<1, 1, 0, c->st>>>(m->S);
   ++c->launches;
   if (grad)
-    CK(spectral_apply<R>(g, m->sw, m->mt, m->sig_t, m->phase, m->D, XIn::Plain, (R*)grad, nullptr, nullptr, c->st,
+    CK(spectral_apply<R>(c->gs, m->sw, m->mt, m->sig_t, m->phase, m->D, XIn::Plain, (R*)grad, nullptr, nullptr, c->st,
                          &c->launches),
        "gradient");
   rve_status s = read_scalars<R>(c);
@@ -824,7 +830,7 @@ rve_status steihaug_once_impl(rve_ctx* c, double Rad, double eta_cg, void* zout,
 template <typename R>
 rve_status apply_impl(rve_ctx* c, const void* v, void* out, bool tangent) {
   Impl<R>* m = impl_of<R>(c);
-  CK(spectral_apply<R>(c->g, m->sw, m->mt, (const R*)v, m->phase, m->D, tangent ? XIn::Tangent : XIn::Plain,
+  CK(spectral_apply<R>(c->gs, m->sw, m->mt, (const R*)v, m->phase, m->D, tangent ? XIn::Tangent : XIn::Plain,
                        (R*)out, nullptr, nullptr, c->st, &c->launches),
      tangent ? "hessp" : "project");
   if (tangent) ++c->hv;
@@ -850,6 +856,7 @@ void rve_default_opts(rve_solver_opts* o) {
   o->precision = 32;
   o->hessian = 0;
   o->passes = 0;
+  o->element = 0;
 }
 
 rve_status rve_create(const int dims[3], int ndim, const uint8_t* phase_ids_dev, const rve_phase* phases, int nphase,
@@ -884,6 +891,18 @@ rve_status rve_create(const int dims[3], int ndim, const uint8_t* phase_ids_dev,
     delete c;
     return fail(nullptr, RVE_ERR_ARG, "hessian must be 0 (secant) or 1 (symmetric consistent)");
   }
+  if (c->opts.element != 0 && c->opts.element != 1) {
+    delete c;
+    return fail(nullptr, RVE_ERR_ARG, "element must be 0 (one element per voxel) or 1 (Kuhn simplices)");
+  }
+  if (c->opts.element == 1 && ndim != 2) {
+    delete c;
+    return fail(nullptr, RVE_ERR_ARG, "element 1 (Kuhn simplices) is built for 2D grids only");
+  }
+  if (c->opts.element == 1 && c->opts.hessian != 0) {
+    delete c;
+    return fail(nullptr, RVE_ERR_ARG, "element 1 (Kuhn simplices) takes the secant Hessian only");
+  }
   if (c->opts.passes < 0 || c->opts.passes > 2) {
     delete c;
     return fail(nullptr, RVE_ERR_ARG, "passes must be 0 (compiled, fused CG), 1 (generic) or 2 (compiled, unfused CG)");
@@ -899,6 +918,15 @@ rve_status rve_create(const int dims[3], int ndim, const uint8_t* phase_ids_dev,
   g.ncomp = ndim == 3 ? 6 : 3;
   g.nvox = (long long)g.nx * g.ny * g.nz;
   g.nrows = (long long)g.ny * g.nz;
+  c->gs = g;
+  if (c->opts.element == 1) {
+    // 2D Kuhn triangles: two strain points per pixel; the spectral passes
+    // transform the six lines c * 2 + q of every pixel
+    c->gs.nq = 2;
+    c->gs.ncomp = 6;
+    g.nq = 2;
+    g.nvox = 2 * c->gs.nvox;
+  }
   cudaError_t e = cudaMallocHost(&c->Sh, sizeof(DevScalars));
   if (e != cudaSuccess) {
     delete c;

@@ -61,22 +61,28 @@ class RVESolver:
         self._ids = ids
         self.phases = [p if isinstance(p, Phase) else Phase(*p) for p in phases]
         self.opts = make_opts(precision, **opts)
+        # strain points per voxel: 2 with the Kuhn-triangle element (2D)
+        self.nq = 2 if self.opts.element == 1 else 1
+        self.fshape = ((self.ncomp, self.nq) if self.nq > 1 else (self.ncomp,)) + self.shape
+        self.sshape = ((self.nq,) if self.nq > 1 else ()) + self.shape
         self._in()
         self.h = B.rve_create(self.dims, self.ndim, ids.data_ptr(), [p.as_tuple() for p in self.phases],
                               self.opts, self.stream.cuda_stream)
 
     # ------------------------------------------------------------ helpers
     def field(self, fill=None):
-        t = torch.empty((self.ncomp,) + self.shape, dtype=self.dtype, device=self.device)
+        """A strain-sized field: (ncomp, [nq,] *grid) of the context's type."""
+        t = torch.empty(self.fshape, dtype=self.dtype, device=self.device)
         if fill is not None:
             t.fill_(fill)
         return t
 
     def scalar_field(self):
-        return torch.empty(self.shape, dtype=self.dtype, device=self.device)
+        """One value per strain point: ([nq,] *grid)."""
+        return torch.empty(self.sshape, dtype=self.dtype, device=self.device)
 
     def _chk(self, t, kind="field"):
-        want = (self.ncomp,) + self.shape if kind == "field" else self.shape
+        want = self.fshape if kind == "field" else self.sshape
         dt = self.dtype
         if t.device != self.device or t.dtype != dt or tuple(t.shape) != want or not t.is_contiguous():
             raise ValueError(f"expected contiguous {dt} {kind} of shape {want} on {self.device}, "

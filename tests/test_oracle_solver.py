@@ -330,3 +330,48 @@ def test_trust_region_radius_and_acceptance_rules(monkeypatch):
         _radius_trace(monkeypatch, Rmax, seen)
     want = {"shrink", "accept_and_shrink", "grow", "cap", "keep", "keep_interior", "accept", "reject_positive"}
     assert want <= seen, want - seen
+
+
+def _laminate_parallel_softening(pa, pb, E):
+    """Closed form of a 50/50 bilayer normal to z under the mean strain
+    eps_xx = E with the other mean components stress-free, layer a damaging
+    (pa.kappa0, pa.kappaf), layer b elastic.  Each layer keeps a uniform
+    strain: eps_xx = E and a common eps_yy = e (in-plane continuity),
+    eps_zz of layer i from sigma_zz = 0, no shear.  The principal strains
+    besides E are compressive, so kappa = E in layer a and its damage
+    follows from E alone; with w_i = (1 - D_i) / 2 and the plane-stress
+    modulus l_i* = 2 l_i m_i / (l_i + 2 m_i), sigma_yy,i = (1 - D_i) (l_i*
+    (E + e) + 2 m_i e) and zero mean sigma_yy give
+    e = -E sum w_i l_i* / sum w_i (l_i* + 2 m_i), and the mean
+    sigma_xx = sum w_i (l_i* (E + e) + 2 m_i E)."""
+    (la, ma), (lb, mb) = oracle.lame(pa.E, pa.nu), oracle.lame(pb.E, pb.nu)
+    k0, kf = pa.kappa0, pa.kappaf
+    Da = 0.0 if E <= k0 else (1.0 if E >= kf else kf * (E - k0) / (E * (kf - k0)))
+    w = np.array([0.5 * (1.0 - Da), 0.5])
+    lam, mu = np.array([la, lb]), np.array([ma, mb])
+    ls = 2.0 * lam * mu / (lam + 2.0 * mu)
+    e = -E * np.sum(w * ls) / np.sum(w * (ls + 2.0 * mu))
+    return float(np.sum(w * (ls * (E + e) + 2.0 * mu * E))), e
+
+
+def test_laminate_parallel_loading_softening_curve():
+    """Sec. 3.3 loading of a bilayer along its layers through the whole
+    softening branch of the damaging layer (D up to 0.99): every increment's
+    mean stress equals the closed form, and the damaging layer carries one
+    uniform damage value."""
+    pa, pb = oracle.Phase(1.0, 0.3, True, 1e-4, 1e-3), oracle.Phase(10.0, 0.2)
+    dims = (4, 4, 8)
+    pm = laminate(dims, axis=2)
+    free = np.array([False, True, True, True, True, True])
+    rve = oracle.RVE(pm, [pa, pb], free_mask=free)
+    inc = 4.5e-5
+    prm = TRParams(eta_eq=1e-10, eta_cg=1e-12, R0=1.0, Rmax=1.0, max_nr=200, max_cg=2000)
+    res = load_path(rve, [np.array([inc, 0, 0, 0, 0, 0])] * 20, prm)
+    assert all(r.converged for r in res["reports"])
+    for n in range(20):
+        sxx, e = _laminate_parallel_softening(pa, pb, (n + 1) * inc)
+        assert abs(res["mean_stress"][n][0] - sxx) <= 1e-9 * abs(sxx), n
+        assert abs(res["mean_strain"][n][1] - e) <= 1e-9 * abs(e), n
+    k = res["kappa"][:4]
+    assert np.allclose(k, 20 * inc, rtol=1e-12)  # layer a: kappa = E everywhere
+    assert np.all(res["kappa"][4:] == 0.0)        # layer b: elastic

@@ -127,19 +127,44 @@ __device__ __forceinline__ float xfwd_rows(float2* buf, const float* __restrict_
   }
   __syncthreads();
   fft_ct<N, NL, kFT, false>(buf, tw);
+  // Separate the two real rows of every packed line (Hermitian symmetry of
+  // real-input spectra) and store the half spectra.  Thread t takes bin
+  // k = t mod (N/2) of the lines p = t div (N/2) + j (256 / (N/2)); the
+  // Nyquist bin of every line goes to threads 0 .. NL-1.  Row and component
+  // of the two halves follow from p alone, so no per-item division by the
+  // half-spectrum length.
   constexpr int NXH = N / 2 + 1;
-  for (int idx = threadIdx.x; idx < NL * NXH; idx += kFT) {
-    const int p = idx / NXH, k = idx - (idx / NXH) * NXH;
-    const float2 zk = buf[k * NL + p];
-    const float2 zm = buf[((N - k) % N) * NL + p];
-    const float2 xa = make_float2((zk.x + zm.x) * 0.5f, (zk.y - zm.y) * 0.5f);
-    const float2 xb = make_float2((zk.y + zm.y) * 0.5f, (zm.x - zk.x) * 0.5f);
+  constexpr int KB = N / 2, GB = kFT / KB, JB = (NL + GB - 1) / GB;
+  const long long plane = nrows * NXH;
+  {
+    const int g = threadIdx.x / KB, k = threadIdx.x - (threadIdx.x / KB) * KB;
+    const int km = k == 0 ? 0 : N - k;
+    if (g < GB) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int rho = 2 * p + h;
-      const int q = rho / NC, c = rho - (rho / NC) * NC;
-      const long long row = row0 + q;
-      if (row < row_end) spec[(c * nrows + row) * NXH + k] = h ? xb : xa;
+      for (int j = 0; j < JB; ++j) {
+        const int p = g + j * GB;
+        if (JB * GB == NL || p < NL) {
+          const float2 zk = buf[k * NL + p], zm = buf[km * NL + p];
+          const float2 xa = make_float2((zk.x + zm.x) * 0.5f, (zk.y - zm.y) * 0.5f);
+          const float2 xb = make_float2((zk.y + zm.y) * 0.5f, (zm.x - zk.x) * 0.5f);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int rho = 2 * p + h;
+            const int q = rho / NC, c = rho - (rho / NC) * NC;
+            if (row0 + q < row_end) spec[c * plane + (row0 + q) * NXH + k] = h ? xb : xa;
+          }
+        }
+      }
+    }
+    if (threadIdx.x < NL) {
+      const int p = threadIdx.x;
+      const float2 z = buf[KB * NL + p];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int rho = 2 * p + h;
+        const int q = rho / NC, c = rho - (rho / NC) * NC;
+        if (row0 + q < row_end) spec[c * plane + (row0 + q) * NXH + KB] = make_float2(h ? z.y : z.x, 0.f);
+      }
     }
   }
   return acc;
@@ -167,41 +192,54 @@ __device__ __forceinline__ void xinv_rows(float2* buf, double* red, const float2
   constexpr int Q = xq<N, NC>();
   constexpr int NL = NC * Q / 2;
   constexpr int NXH = N / 2 + 1;
-  constexpr int HALF = N / 2;
-  // each half-spectrum entry kk of the two real lines packed in line p is
-  // read once and fills both buf[kk] and buf[N - kk] (Hermitian symmetry)
-  constexpr int LITEMS = NL * NXH;
-  constexpr int LSTEPS = (LITEMS + kFT - 1) / kFT;
-  constexpr int LB = LSTEPS < 4 ? LSTEPS : 4;
-  for (int s0 = 0; s0 < LSTEPS; s0 += LB) {
-    float2 xh[LB][2];
+  // Each half-spectrum entry kk of the two real rows packed in line p is read
+  // once and fills both buf[kk] and buf[N - kk] (Hermitian symmetry).
+  // Thread t takes bin kk = t mod (N/2) of the lines p = t div (N/2) + j
+  // (256 / (N/2)), all its loads issued before its stores; the Nyquist bin of
+  // every line goes to threads 0 .. NL-1.
+  constexpr int KB = N / 2, GB = kFT / KB, JB = (NL + GB - 1) / GB;
+  const long long plane = nrows * NXH;
+  {
+    const int g = threadIdx.x / KB, kk = threadIdx.x - (threadIdx.x / KB) * KB;
+    if (g < GB) {
+      float2 xh[JB][2];
 #pragma unroll
-    for (int b = 0; b < LB; ++b) {
-      const int idx = threadIdx.x + (s0 + b) * kFT;
-      const int p = idx / NXH, kk = idx - (idx / NXH) * NXH;
+      for (int j = 0; j < JB; ++j) {
+        const int p = g + j * GB;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int rho = 2 * p + h;
+          const int q = rho / NC, c = rho - (rho / NC) * NC;
+          const float2* src = spec + c * plane + (row0 + q) * NXH + kk;
+          xh[j][h] = ((JB * GB == NL || p < NL) && row0 + q < row_end) ? (L2LOAD ? __ldcg(src) : *src)
+                                                                       : make_float2(0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < JB; ++j) {
+        const int p = g + j * GB;
+        if (JB * GB == NL || p < NL) {
+          float2 a = xh[j][0], c2 = xh[j][1];
+          if (kk == 0) {
+            a.y = 0.f;
+            c2.y = 0.f;
+          }
+          buf[kk * NL + p] = make_float2(a.x - c2.y, a.y + c2.x);
+          if (kk != 0) buf[(N - kk) * NL + p] = make_float2(a.x + c2.y, c2.x - a.y);
+        }
+      }
+    }
+    if (threadIdx.x < NL) {
+      const int p = threadIdx.x;
+      float2 xn[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int rho = 2 * p + h;
         const int q = rho / NC, c = rho - (rho / NC) * NC;
-        const long long row = row0 + q;
-        const float2* src = spec + (c * nrows + row) * NXH + kk;
-        xh[b][h] = (s0 + b < LSTEPS && idx < LITEMS && row < row_end) ? (L2LOAD ? __ldcg(src) : *src)
-                                                                      : make_float2(0.f, 0.f);
+        const float2* src = spec + c * plane + (row0 + q) * NXH + KB;
+        xn[h] = row0 + q < row_end ? (L2LOAD ? __ldcg(src) : *src) : make_float2(0.f, 0.f);
       }
-    }
-#pragma unroll
-    for (int b = 0; b < LB; ++b) {
-      const int idx = threadIdx.x + (s0 + b) * kFT;
-      if (s0 + b < LSTEPS && idx < LITEMS) {
-        const int p = idx / NXH, kk = idx - (idx / NXH) * NXH;
-        float2 a = xh[b][0], c2 = xh[b][1];
-        if (kk == 0 || kk == HALF) {
-          a.y = 0.f;
-          c2.y = 0.f;
-        }
-        buf[kk * NL + p] = make_float2(a.x - c2.y, a.y + c2.x);
-        if (kk != 0 && kk != HALF) buf[(N - kk) * NL + p] = make_float2(a.x + c2.y, c2.x - a.y);
-      }
+      buf[KB * NL + p] = make_float2(xn[0].x, xn[1].x);  // imaginary parts of the Nyquist bin dropped
     }
   }
   __syncthreads();

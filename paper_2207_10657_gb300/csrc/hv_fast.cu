@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kFT)
 }
 
 template <int N, int NC, bool DOT, bool CG = false>
-__global__ void __launch_bounds__(kFT)
+__global__ void __launch_bounds__(kFT, 4)
     kf_xinv(const float2* __restrict__ spec, float* __restrict__ out, const float* __restrict__ dotw,
             double* __restrict__ partials, const long long nrows, const long long nvox,
             const float2* __restrict__ tw, const float scale, const bool self_dot, float* __restrict__ cz = nullptr,
@@ -106,19 +106,23 @@ __global__ void __launch_bounds__(zthreads<N>(), zminblocks<N>())
     __syncthreads();
     fft_ct<N, NL, NT, false>(buf, tw);
   }
-  const float2 ay = gay[ky], dy = gdy[ky];
-  for (int pt = threadIdx.x; pt < N * TX; pt += NT) {
-    const int z = pt / TX, t = pt - (pt / TX) * TX;
-    const int kx = kx0 + t;
-    if (t >= tv) continue;
-    float2 m[6];
+  // every point of a thread has the same column t (NT is a multiple of TX):
+  // the x and y factors of the symbol are formed once
+  static_assert(NT % TX == 0, "z-pass threads must be a multiple of its columns");
+  const int t = threadIdx.x % TX, kx = kx0 + t;
+  if (t < tv) {
+    const float2 ay = gay[ky], dy = gdy[ky], ax = gax[kx], dx = gdx[kx];
+    const float2 fx = cmul(dx, ay), fy = cmul(ax, dy), fz = cmul(ax, ay);
+    const bool kxy0 = kx == 0 && ky == 0;
+    for (int z = threadIdx.x / TX; z < N; z += NT / TX) {
+      float2 m[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) m[c] = buf[z * NL + c * TX + t];
-    const float2 ax = gax[kx], dx = gdx[kx], az = gaz[z], dz = gdz[z];
-    project3<float>(m, cmul(cmul(dx, ay), az), cmul(cmul(ax, dy), az), cmul(cmul(ax, ay), dz),
-                    kx == 0 && ky == 0 && z == 0, free_mask);
+      for (int c = 0; c < 6; ++c) m[c] = buf[z * NL + c * TX + t];
+      const float2 az = gaz[z];
+      project3<float>(m, cmul(fx, az), cmul(fy, az), cmul(fz, gdz[z]), kxy0 && z == 0, free_mask);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) buf[z * NL + c * TX + t] = m[c];
+      for (int c = 0; c < 6; ++c) buf[z * NL + c * TX + t] = m[c];
+    }
   }
   __syncthreads();
   // inverse z transform

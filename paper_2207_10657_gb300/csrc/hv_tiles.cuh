@@ -26,6 +26,32 @@ template <int N> constexpr int ytx() { return (kFBudget / N) < 16 ? (kFBudget / 
 template <int N> constexpr int ztx() { return N <= 64 ? 16 : 4; }
 template <int N> constexpr int zthreads() { return N >= 512 ? 512 : 256; }
 template <int N> constexpr int zminblocks() { return N >= 512 ? 1 : 3; }
+// Items (rho, x) -- real row rho of a tile of NROW rows, element x -- as
+// thread threadIdx.x takes them, item i = 0 .. COUNT-1.  Where N divides the
+// 256 threads (or 256 divides N) a thread keeps one x (two for N = 512) and
+// steps through the rows, so that rho is a compile-time constant for
+// N >= 256 and the row / component split of rho costs nothing; other N take
+// consecutive elements of the flattened tile.
+template <int N, int NROW> struct RowItems {
+  static constexpr bool REG = (kFT % N == 0) || (N % kFT == 0);
+  static constexpr int XR = N >= kFT ? 1 : kFT / N;  // rows per sweep of the block
+  static constexpr int XH = N >= kFT ? N / kFT : 1;  // elements per row and thread
+  static constexpr int NJ = (NROW + XR - 1) / XR;
+  static constexpr int COUNT = REG ? NJ * XH : (NROW * N + kFT - 1) / kFT;
+  __device__ __forceinline__ static void at(int i, int& rho, int& x) {
+    if constexpr (REG) {
+      const int j = i / XH, h = i - (i / XH) * XH;
+      rho = (N >= kFT ? 0 : (int)threadIdx.x / N) + j * XR;
+      x = (N >= kFT ? (int)threadIdx.x : (int)threadIdx.x % N) + h * kFT;
+    } else {
+      const int idx = threadIdx.x + i * kFT;
+      rho = idx / N;
+      x = idx - rho * N;
+    }
+  }
+  __device__ __forceinline__ static bool valid(int rho, int) { return rho < NROW; }
+};
+
 
 // ------------------------------------------------------------ x forward
 // One x-forward tile: the voxel rows [row0, row_end) (at most xq rows),
@@ -244,26 +270,29 @@ __device__ __forceinline__ void xinv_rows(float2* buf, double* red, const float2
   }
   __syncthreads();
   fft_ct<N, NL, kFT, true>(buf, tw);
+  // The Q * NC real rows of the tile leave shared memory as items (rho, x):
+  // see RowItems.  A thread's partial sums are plain FP32 over its ~30 items,
+  // combined in FP64 across the block and the grid.
+  using RI = RowItems<N, Q * NC>;
+  constexpr int SB = CG ? 4 : 8;  // items whose loads are in flight together
+  constexpr int NG = (RI::COUNT + SB - 1) / SB;
   if constexpr (CG) {
     const int status = *cstatus;
     const bool run = status == 0, exit_tau = status == 2 || status == 3;  // running / boundary, negative curvature
     const float al = (float)*calpha, ta = (float)*ctau;
-    KSum<float> cs[3];
-    constexpr int SITEMS = Q * NC * N;
-    constexpr int SSTEPS = (SITEMS + kFT - 1) / kFT;
-    constexpr int SB = SSTEPS < 4 ? SSTEPS : 4;
-    for (int s0 = 0; s0 < SSTEPS; s0 += SB) {
+    float cs[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
       float o[SB], zv[SB], rv[SB], dv[SB];
       long long off[SB];
       bool ok[SB];
 #pragma unroll
       for (int b = 0; b < SB; ++b) {
-        const int idx = threadIdx.x + (s0 + b) * kFT;
-        const int rho = idx / N, x = idx - (idx / N) * N;
+        int rho, x;
+        RI::at(g * SB + b, rho, x);
         const int q = rho / NC, c = rho - (rho / NC) * NC;
-        const long long row = row0 + q;
-        ok[b] = (s0 + b < SSTEPS) && idx < SITEMS && row < row_end && (run || exit_tau);
-        off[b] = c * nvox + row * N + x;
+        ok[b] = g * SB + b < RI::COUNT && RI::valid(rho, x) && row0 + q < row_end && (run || exit_tau);
+        off[b] = c * nvox + (row0 + q) * N + x;
         o[b] = ok[b] ? reinterpret_cast<const float*>(&buf[x * NL + (rho >> 1)])[rho & 1] * scale : 0.f;
         zv[b] = ok[b] ? cz[off[b]] : 0.f;
         dv[b] = ok[b] ? __ldg(cd + off[b]) : 0.f;
@@ -276,36 +305,33 @@ __device__ __forceinline__ void xinv_rows(float2* buf, double* red, const float2
           const float zn = zv[b] + al * dv[b], rn = rv[b] + al * o[b];
           cz[off[b]] = zn;
           cr[off[b]] = rn;
-          cs[0].add(rn * rn);
-          cs[1].add(rn * rv[b]);
-          cs[2].add(zn * zn);
+          cs[0] += rn * rn;
+          cs[1] += rn * rv[b];
+          cs[2] += zn * zn;
         } else {
           cz[off[b]] = zv[b] + ta * dv[b];
         }
       }
     }
-    double v3[3] = {cs[0].value(), cs[1].value(), cs[2].value()};
+    double v3[3] = {(double)cs[0], (double)cs[1], (double)cs[2]};
     block_sum<3>(v3, red);
     if (threadIdx.x == 0)
       for (int k = 0; k < 3; ++k) partials[3 * pidx + k] = v3[k];
     return;
   }
-  KSum<float> acc;
-  constexpr int SITEMS = Q * NC * N;
-  constexpr int SSTEPS = (SITEMS + kFT - 1) / kFT;
-  constexpr int SB = SSTEPS < 8 ? SSTEPS : 8;
-  for (int s0 = 0; s0 < SSTEPS; s0 += SB) {
+  float acc = 0.f;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
     float o[SB], w[SB];
     long long off[SB];
     bool ok[SB];
 #pragma unroll
     for (int b = 0; b < SB; ++b) {
-      const int idx = threadIdx.x + (s0 + b) * kFT;
-      const int rho = idx / N, x = idx - (idx / N) * N;
+      int rho, x;
+      RI::at(g * SB + b, rho, x);
       const int q = rho / NC, c = rho - (rho / NC) * NC;
-      const long long row = row0 + q;
-      ok[b] = (s0 + b < SSTEPS) && idx < SITEMS && row < row_end;
-      off[b] = c * nvox + row * N + x;
+      ok[b] = g * SB + b < RI::COUNT && RI::valid(rho, x) && row0 + q < row_end;
+      off[b] = c * nvox + (row0 + q) * N + x;
       o[b] = ok[b] ? reinterpret_cast<const float*>(&buf[x * NL + (rho >> 1)])[rho & 1] * scale : 0.f;
       w[b] = (DOT && ok[b]) ? (self_dot ? o[b] : __ldg(dotw + off[b])) : 0.f;
     }
@@ -313,12 +339,12 @@ __device__ __forceinline__ void xinv_rows(float2* buf, double* red, const float2
     for (int b = 0; b < SB; ++b) {
       if (ok[b]) {
         out[off[b]] = o[b];
-        if (DOT) acc.add(o[b] * w[b]);
+        if (DOT) acc += o[b] * w[b];
       }
     }
   }
   if (DOT) {
-    double v[1] = {acc.value()};
+    double v[1] = {(double)acc};
     block_sum<1>(v, red);
     if (threadIdx.x == 0) partials[pidx] = v[0];
   }

@@ -7,10 +7,14 @@
 namespace rve {
 
 // ------------------------------------------------------------ projection
-// Ghat(k) : zeta for one frequency, Mandel components m (complex).
-// n = Dhat/|Dhat|, v = zeta n*, s = n*^T zeta n*,
-// Ghat:zeta = n (x) v + v (x) n - s n (x) n.  Ghat = 0 where Dhat = 0
-// (k != 0); Ghat(0) keeps the stress-controlled (free) components.
+// Ghat(k) : zeta for one frequency, Mandel components m (complex), from the
+// unnormalised symbol D = Dhat(k).  With n = D/|D|, v = zeta n* and
+// s = n*^T zeta n*, Ghat:zeta = n (x) v + v (x) n - s n (x) n.  Written with
+// D itself: v' = zeta D*, s' = D*^T v', w = v' - (s' / (2 |D|^2)) D, and
+// Ghat:zeta = (D (x) w + w (x) D) / |D|^2 -- the same operator, one
+// reciprocal instead of a normalisation, and two products per output entry
+// instead of four.  Ghat = 0 where D = 0 (k != 0); Ghat(0) keeps the
+// stress-controlled (free) components.
 template <typename R>
 __device__ __forceinline__ void project3(Cx<R> (&m)[6], Cx<R> d0, Cx<R> d1, Cx<R> d2, bool k0,
                                          unsigned free_mask) {
@@ -27,24 +31,24 @@ __device__ __forceinline__ void project3(Cx<R> (&m)[6], Cx<R> d0, Cx<R> d1, Cx<R
     for (int c = 0; c < 6; ++c) m[c] = C{0, 0};
     return;
   }
-  const R inv = (R)1 / sqrt(n2);
-  const C n[3] = {cscale(d0, inv), cscale(d1, inv), cscale(d2, inv)};
+  const R inv = (R)1 / n2;
   const R is2 = (R)0.70710678118654752440, s2 = (R)1.41421356237309504880;
   const C t00 = m[0], t11 = m[1], t22 = m[2];
   const C t12 = cscale(m[3], is2), t02 = cscale(m[4], is2), t01 = cscale(m[5], is2);
-  // v_i = sum_j T_ij conj(n_j)
-  const C v0 = cadd(cadd(cmulc(t00, n[0]), cmulc(t01, n[1])), cmulc(t02, n[2]));
-  const C v1 = cadd(cadd(cmulc(t01, n[0]), cmulc(t11, n[1])), cmulc(t12, n[2]));
-  const C v2 = cadd(cadd(cmulc(t02, n[0]), cmulc(t12, n[1])), cmulc(t22, n[2]));
-  // s = sum_i conj(n_i) v_i
-  const C s = cadd(cadd(cmulc(v0, n[0]), cmulc(v1, n[1])), cmulc(v2, n[2]));
-  auto o = [&](C ni, C nj, C vi, C vj) { return csub(cadd(cmul(ni, vj), cmul(vi, nj)), cmul(s, cmul(ni, nj))); };
-  m[0] = o(n[0], n[0], v0, v0);
-  m[1] = o(n[1], n[1], v1, v1);
-  m[2] = o(n[2], n[2], v2, v2);
-  m[3] = cscale(o(n[1], n[2], v1, v2), s2);
-  m[4] = cscale(o(n[0], n[2], v0, v2), s2);
-  m[5] = cscale(o(n[0], n[1], v0, v1), s2);
+  // v_i = sum_j T_ij conj(D_j)
+  const C v0 = cadd(cadd(cmulc(t00, d0), cmulc(t01, d1)), cmulc(t02, d2));
+  const C v1 = cadd(cadd(cmulc(t01, d0), cmulc(t11, d1)), cmulc(t12, d2));
+  const C v2 = cadd(cadd(cmulc(t02, d0), cmulc(t12, d1)), cmulc(t22, d2));
+  // s = sum_i conj(D_i) v_i, scaled by -1 / (2 |D|^2)
+  const C sh = cscale(cadd(cadd(cmulc(v0, d0), cmulc(v1, d1)), cmulc(v2, d2)), (R)-0.5 * inv);
+  const C w0 = cadd(v0, cmul(sh, d0)), w1 = cadd(v1, cmul(sh, d1)), w2 = cadd(v2, cmul(sh, d2));
+  const R i2 = (R)2 * inv, is = s2 * inv;
+  m[0] = cscale(cmul(d0, w0), i2);
+  m[1] = cscale(cmul(d1, w1), i2);
+  m[2] = cscale(cmul(d2, w2), i2);
+  m[3] = cscale(cadd(cmul(d1, w2), cmul(w1, d2)), is);
+  m[4] = cscale(cadd(cmul(d0, w2), cmul(w0, d2)), is);
+  m[5] = cscale(cadd(cmul(d0, w1), cmul(w0, d1)), is);
 }
 
 template <typename R>

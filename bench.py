@@ -1019,11 +1019,14 @@ def run_probe(args):
     from paper_2207_10657_gb300 import build as _build
     _build.build()
     if args.probe == "step":
-        from paper_2207_10657_gb300 import RVESolver
+        from paper_2207_10657_gb300 import RVESolver, binding
         from synth import random_spheres
         dims = (256, 256, 128)
         pm = random_spheres(dims, count=100, rmin=4, rmax=10, seed=0)
         s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, eta_eq=1e-6, eta_cg=1e-2, max_nr=50)
+        # the CG iterations stepped from the host: the same kernels, each a
+        # separate launch a profiler can take (the device loop's are graph nodes)
+        binding.rve_set_device_loop(s.h, False)
         r = s.solve_step([0, 0, INC, 0, 0, 0], free_mask=FREE, raise_on_error=False)
         torch.cuda.synchronize()
         print("probe step", r["converged"], r["hv_products"], s.launch_count)

@@ -23,9 +23,9 @@ template <int N, int NC> constexpr int xq() {
   return ((nl & 1) == 0 && q2 > ((NC & 1) ? 2 : 1)) ? q2 - ((NC & 1) ? 2 : 1) : q2;
 }
 template <int N> constexpr int ytx() { return (kFBudget / N) < 16 ? (kFBudget / N) : 16; }
-template <int N> constexpr int ztx() { return N <= 64 ? 16 : 4; }
-template <int N> constexpr int zthreads() { return N >= 512 ? 512 : 256; }
-template <int N> constexpr int zminblocks() { return N >= 512 ? 1 : 3; }
+template <int N> constexpr int ztx() { return N <= 64 ? 16 : (N <= 256 ? 8 : 4); }
+template <int N> constexpr int zthreads() { return N >= 512 || (N >= 128 && N <= 256) ? 512 : 256; }
+template <int N> constexpr int zminblocks() { return N >= 512 ? 1 : (N >= 128 && N <= 256 ? 2 : 3); }
 // Items (rho, x) -- real row rho of a tile of NROW rows, element x -- as
 // thread threadIdx.x takes them, item i = 0 .. COUNT-1.  Where N divides the
 // 256 threads (or 256 divides N) a thread keeps one x (two for N = 512) and

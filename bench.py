@@ -472,6 +472,10 @@ def run_gpu(args):
     hv_only_ms = sum(stats[k][1] for k in hv_passes)
     hv_bytes = sum(_pass_bytes(n, k) for k in hv_passes)
     nprod = max(stats["z_proj"][0], 1)
+    # DRAM bytes of the same passes from the committed ncu record (None if it
+    # was taken on other kernel sources)
+    ncu_parts = [_traffic(k, n) for k in hv_passes]
+    ncu_bytes = sum(ncu_parts) if ncu_parts and all(x is not None for x in ncu_parts) else None
 
     # ---------------- a load step at the damage onset (past kappa0), where the
     # Newton iterations and not the product dominate: both Hessians
@@ -529,7 +533,9 @@ def run_gpu(args):
                         "achieved": hv_bytes / (hv_only_ms / nprod / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": hv_bytes / (hv_only_ms / nprod / 1e3) / 1e9 / peak,
                         "algorithmic_bytes_per_product": hv_bytes,
-                        "product_alone_bytes": hv_bytes - _pass_bytes(n, "x_inv") + _pass_bytes(n, "x_inv_plain")},
+                        "product_alone_bytes": hv_bytes - _pass_bytes(n, "x_inv") + _pass_bytes(n, "x_inv_plain"),
+                        "ncu_dram_bytes_per_product": ncu_bytes,
+                        "ncu_frac": (ncu_bytes / (hv_only_ms / nprod / 1e3) / 1e9 / peak) if ncu_bytes else None},
         "compulsory_fraction": {"bytes_per_voxel": 53, "frac": 53 * nvox / (hv_only_ms / nprod / 1e3) / 1e9 / peak},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 6 * nvox * 4,

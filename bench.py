@@ -110,6 +110,8 @@ def _args():
     p.add_argument("--probe", choices=["step", "fno"], default=None,
                    help="untimed small case for profilers: 'step' = one load step of a 256x256x128 sphere cell, "
                         "'fno' = three training iterations of the spectral neural operator at 64^3, batch 4")
+    p.add_argument("--probe-dims", default="256,256,128",
+                   help="probe step: grid (nx,ny,nz); 256,128,256 gives the length-256 z pass the benchmark runs")
     p.add_argument("--batch-max-nr", type=int, default=50,
                    help="Newton cap per member for batch96 (bounds the work of members that localise)")
     return p.parse_args()
@@ -1027,7 +1029,7 @@ def run_probe(args):
     if args.probe == "step":
         from paper_2207_10657_gb300 import RVESolver, binding
         from synth import random_spheres
-        dims = (256, 256, 128)
+        dims = tuple(int(x) for x in args.probe_dims.split(","))
         pm = random_spheres(dims, count=100, rmin=4, rmax=10, seed=0)
         s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, eta_eq=1e-6, eta_cg=1e-2, max_nr=50)
         # the CG iterations stepped from the host: the same kernels, each a

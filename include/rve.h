@@ -22,9 +22,11 @@
  *    at offset ((c*Nz + z)*Ny + y)*Nx + x, x fastest.  Components are
  *    Mandel-orthonormal: 3D (11, 22, 33, sqrt2*23, sqrt2*13, sqrt2*12),
  *    2D plane strain (11, 22, sqrt2*12).  ncomp = 6 (3D) or 3 (2D).  With
- *    the triangle element (rve_solver_opts.element = 1) a field has two
- *    strain points per pixel: ncomp x 2 x Nvox, element (c, q, y, x) at
- *    ((c*2 + q)*Ny + y)*Nx + x, and per-point scalar fields 2 x Nvox.
+ *    the simplex element (rve_solver_opts.element = 1) a field has nq
+ *    strain points per voxel (nq = 2 triangles in 2D, 6 tetrahedra in
+ *    3D): ncomp x nq x Nvox, element (c, q, [z,] y, x) at
+ *    (((c*nq + q)*Nz + z)*Ny + y)*Nx + x, and per-point scalar fields
+ *    nq x Nvox.
  *  - Real type: float when the context was created with precision 32,
  *    double with precision 64.  Pointers named *_dev are DEVICE pointers,
  *    owned by the caller, 16-byte aligned, read/written on the context's
@@ -106,15 +108,20 @@ typedef struct {
   int element;        /* finite-element gradient the projection is built from
                          (Sec. 2.1, Eq. (9)): 0: one bilinear / trilinear
                          element per voxel, one quadrature point (default);
-                         1: linear triangles, every pixel split along its main
-                         diagonal into the two triangles of axis order (x, y)
-                         and (y, x), one quadrature point each -- 2D only,
-                         secant Hessian only.  With 1 every strain-sized
-                         field holds ncomp x 2 x Nvox reals, layout
-                         [c][q][y][x] (triangle q = 0 for (x, y), 1 for
-                         (y, x)), and every per-point scalar field (history,
-                         damage) 2 x Nvox; the mean strain and stress average
-                         over all triangles. */
+                         1: linear simplices, every voxel split along its
+                         main diagonal into the simplices of the axis
+                         permutations (Kuhn), one quadrature point each: in
+                         2D the two triangles of axis order (x, y) and (y, x),
+                         in 3D the six tetrahedra of the permutations of
+                         (x, y, z) in lexicographic order; secant Hessian
+                         only.  With 1 every strain-sized field holds
+                         ncomp x nq x Nvox reals (nq = 2 or 6), layout
+                         [c][q][z][y][x] (q the simplex in the order above),
+                         and every per-point scalar field (history, damage)
+                         nq x Nvox; the mean strain and stress average over
+                         all simplices.  3D runs on the generic passes and
+                         takes Nx <= 227 and Nz <= 341 (FP32) / 177 (FP64);
+                         rve_create returns RVE_ERR_ARG past that. */
 } rve_solver_opts;
 
 /* Per-load-step statistics. */

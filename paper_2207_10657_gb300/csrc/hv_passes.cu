@@ -108,7 +108,7 @@ cudaError_t spectral_setup(const GridDesc& g, SpecWork<R>& w) {
   // z + projection (3D) or y + projection (2D)
   if (g.ndim == 3) {
     const int ez = std::min(kZThreads * kZEpt, (int)(kSmemCap / sizeof(C)));
-    w.tz = std::max(1, std::min(pow2_floor(std::max(1, ez / (6 * g.nz))), 16));
+    w.tz = std::max(1, std::min(pow2_floor(std::max(1, ez / (g.ncomp * g.nz))), 16));
   } else {
     const int e2 = std::min(kYThreads * kYEpt, (int)(kSmemCap / sizeof(C)));
     w.tz = std::max(1, std::min(pow2_floor(std::max(1, e2 / (g.ncomp * g.ny))), 64));
@@ -146,7 +146,7 @@ cudaError_t spectral_plan(const GridDesc& g, SpecWork<R>& w) {
   w.ty = std::max(1, std::min(pow2_floor(std::max(1, ey / g.ny)), 64));
   if (g.ndim == 3) {
     const int ez = std::min(kZThreads * kZEpt, (int)(kSmemCap / sizeof(C)));
-    w.tz = std::max(1, std::min(pow2_floor(std::max(1, ez / (6 * g.nz))), 16));
+    w.tz = std::max(1, std::min(pow2_floor(std::max(1, ez / (g.ncomp * g.nz))), 16));
   } else {
     const int e2 = std::min(kYThreads * kYEpt, (int)(kSmemCap / sizeof(C)));
     w.tz = std::max(1, std::min(pow2_floor(std::max(1, e2 / (g.ncomp * g.ny))), 64));
@@ -186,7 +186,7 @@ static cudaError_t spectral_middle(const GridDesc& g, SpecWork<R>& w, cudaStream
     const dim3 yg((g.nxh + w.ty - 1) / w.ty, g.nz, g.ncomp);
     const size_t ysm = (size_t)w.ty * g.ny * sizeof(C);
     const dim3 zg((g.nxh + w.tz - 1) / w.tz, g.ny);
-    const size_t zsm = (size_t)6 * w.tz * g.nz * sizeof(C);
+    const size_t zsm = (size_t)g.ncomp * w.tz * g.nz * sizeof(C);
     for (int pass = 0; pass < 3; ++pass) {
       e = cudaErrorNotSupported;
       PassScope ps(w.timer, st, pass == 0 ? PASS_YFWD : (pass == 1 ? PASS_ZPROJ : PASS_YINV));

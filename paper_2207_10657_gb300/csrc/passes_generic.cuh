@@ -35,21 +35,37 @@ __device__ __forceinline__ void xfwd_body(const R* __restrict__ in, const uint8_
   for (int idx = threadIdx.x; idx < Q * nx; idx += blockDim.x) {
     const int q = idx / nx, x = idx - q * nx;
     const long long row = row0 + q;
+    if (g.nq > 1) {
+      // Kuhn simplices: line c * nq + p is Mandel component c of simplex p,
+      // whose damage is dmg[p * nvox + vox]; the tangent acts per simplex
+      const int nqp = g.nq, nm = nc / nqp;
+      const long long vox = row * nx + x;
+      for (int p = 0; p < nqp; ++p) {
+        R m[6] = {0, 0, 0, 0, 0, 0};
+        if (row < g.nrows) {
+          for (int c = 0; c < nm; ++c) m[c] = in[(c * nqp + p) * g.nvox + vox];
+          if (MODE == 1) {
+            const int ph = phase[vox];
+            const R keep = (R)1 - dmg[p * g.nvox + vox];
+            const R lam = mt.lam[ph] * keep, two_mu = (R)2 * mt.mu[ph] * keep;
+            R tr = 0;
+            for (int i = 0; i < nd; ++i) tr += m[i];
+            for (int c = 0; c < nm; ++c) m[c] = two_mu * m[c] + (c < nd ? lam * tr : (R)0);
+          }
+        }
+        for (int c = 0; c < nm; ++c) {
+          const int rho = q * nc + c * nqp + p;
+          R* slot = reinterpret_cast<R*>(&buf[(rho >> 1) * nx + x]) + (rho & 1);
+          *slot = m[c];
+        }
+      }
+      continue;
+    }
     R val[6] = {0, 0, 0, 0, 0, 0};
     if (row < g.nrows) {
       const long long vox = row * nx + x;
       for (int c = 0; c < nc; ++c) val[c] = in[c * g.nvox + vox];
-      if (MODE == 1 && g.nq == 2) {
-        // 2D Kuhn triangles: line c * 2 + q is Mandel component c of triangle
-        // q, whose damage is dmg[q * nvox + vox]
-        const int ph = phase[vox];
-        for (int q2 = 0; q2 < 2; ++q2) {
-          const R keep = (R)1 - dmg[q2 * g.nvox + vox];
-          const R lam = mt.lam[ph] * keep, two_mu = (R)2 * mt.mu[ph] * keep;
-          const R tr = val[q2] + val[2 + q2];
-          for (int c = 0; c < 3; ++c) val[2 * c + q2] = two_mu * val[2 * c + q2] + (c < 2 ? lam * tr : (R)0);
-        }
-      } else if (MODE == 1) {
+      if (MODE == 1) {
         const int ph = phase[vox];
         const R keep = (R)1 - dmg[vox];
         const R lam = mt.lam[ph] * keep, two_mu = (R)2 * mt.mu[ph] * keep;
@@ -145,22 +161,29 @@ __device__ __forceinline__ void zproj_body(Cx<R>* __restrict__ spec, const GridD
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int nz = g.nz, ny = g.ny, nxh = g.nxh;
+  const int ncl = g.ncomp;  // lines per column: 6, or 36 for Kuhn tetrahedra
   const int kx0 = bx * TX, ky = by;
   const int tv = min(TX, nxh - kx0);
   const int plane = nz * TX;
-  for (int idx = threadIdx.x; idx < 6 * plane; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < ncl * plane; idx += blockDim.x) {
     const int c = idx / plane, rem = idx - c * plane;
     const int z = rem / TX, t = rem - z * TX;
     buf[idx] = t < tv ? spec[(((long long)c * nz + z) * ny + ky) * nxh + kx0 + t] : C{0, 0};
   }
   __syncthreads();
   const LineMap lm{TX, plane, 1, TX};
-  fft_lines<kZEpt, false, true>(buf, pz, 6 * TX, lm, tw);
+  fft_lines<kZEpt, false, true>(buf, pz, ncl * TX, lm, tw);
   const C ay = gay[ky], dy = gdy[ky];
   for (int pt = threadIdx.x; pt < plane; pt += blockDim.x) {
     const int z = pt / TX, t = pt - z * TX;
     const int kx = kx0 + t;
     if (t >= tv) continue;
+    if (ncl == 36) {
+      const C d[3] = {gdx[kx], dy, gdz[z]};
+      const C e[3] = {C{(R)1 + d[0].x, d[0].y}, C{(R)1 + d[1].x, d[1].y}, C{(R)1 + d[2].x, d[2].y}};
+      project_simplex3<R>(buf + pt, plane, e, d, kx == 0 && ky == 0 && z == 0, free_mask);
+      continue;
+    }
     C m[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) m[c] = buf[c * plane + pt];
@@ -173,8 +196,8 @@ __device__ __forceinline__ void zproj_body(Cx<R>* __restrict__ spec, const GridD
     for (int c = 0; c < 6; ++c) buf[c * plane + pt] = m[c];
   }
   __syncthreads();
-  fft_lines<kZEpt, true, true>(buf, pz, 6 * TX, lm, tw);
-  for (int idx = threadIdx.x; idx < 6 * plane; idx += blockDim.x) {
+  fft_lines<kZEpt, true, true>(buf, pz, ncl * TX, lm, tw);
+  for (int idx = threadIdx.x; idx < ncl * plane; idx += blockDim.x) {
     const int c = idx / plane, rem = idx - c * plane;
     const int z = rem / TX, t = rem - z * TX;
     if (t < tv) spec[(((long long)c * nz + z) * ny + ky) * nxh + kx0 + t] = buf[idx];

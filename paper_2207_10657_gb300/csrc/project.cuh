@@ -133,4 +133,92 @@ __device__ __forceinline__ void project_simplex2(Cx<R> (&m)[6], Cx<R> ex, Cx<R> 
   }
 }
 
+// Ghat(k) for the 3D Kuhn tetrahedra (every voxel split along its main
+// diagonal into the six tetrahedra of the axis permutations pi, in
+// lexicographic order of pi; Sec. 2.1 builds the projection from any FE
+// gradient).  The 36 lines c * 6 + q -- Mandel component c (11, 22, 33,
+// sqrt2*23, sqrt2*13, sqrt2*12) of tetrahedron q -- sit at p[(c * 6 + q) *
+// stride].  Tetrahedron pi has vertices v0 = 0, v_j = v_{j-1} + e_{pi_j};
+// its derivative symbol along pi_j is e^{i (th_{pi_1} + ... + th_{pi_{j-1}})}
+// (e^{i th_{pi_j}} - 1).  As for the triangles: b = B^H m, a = M^-1 b with
+// the 3 x 3 Hermitian M = B^H B (non-singular for k != 0), m = B a; at
+// k = 0 the free components keep their tetrahedron average and the
+// strain-controlled ones vanish.  e[a]: e^{i th_a}; d[a]: e^{i th_a} - 1
+// (exact zero at k = 0).
+template <typename R>
+__device__ __forceinline__ void project_simplex3(Cx<R>* p, const int stride, const Cx<R> (&e)[3],
+                                                 const Cx<R> (&d)[3], bool k0, unsigned free_mask) {
+  using C = Cx<R>;
+  constexpr int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  if (k0) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      C avg{0, 0};
+      if ((free_mask >> c) & 1u) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) avg = cadd(avg, p[(c * 6 + q) * stride]);
+        avg = cscale(avg, (R)1 / (R)6);
+      }
+#pragma unroll
+      for (int q = 0; q < 6; ++q) p[(c * 6 + q) * stride] = avg;
+    }
+    return;
+  }
+  auto symbol = [&](int q, C (&D)[3]) {
+    C pre{1, 0};
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const int a = kPerm[q][s];
+      D[a] = cmul(pre, d[a]);
+      pre = cmul(pre, e[a]);
+    }
+  };
+  const R is2 = (R)0.70710678118654752440;
+  R m00 = 0, m11 = 0, m22 = 0;
+  C m01{0, 0}, m02{0, 0}, m12{0, 0}, b0{0, 0}, b1{0, 0}, b2{0, 0};
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    C D[3];
+    symbol(q, D);
+    const R a0 = D[0].x * D[0].x + D[0].y * D[0].y, a1 = D[1].x * D[1].x + D[1].y * D[1].y,
+            a2 = D[2].x * D[2].x + D[2].y * D[2].y;
+    m00 += a0 + (R)0.5 * (a1 + a2);
+    m11 += a1 + (R)0.5 * (a0 + a2);
+    m22 += a2 + (R)0.5 * (a0 + a1);
+    m01 = cadd(m01, cscale(cmulc(D[0], D[1]), (R)0.5));  // D0 conj(D1) / 2
+    m02 = cadd(m02, cscale(cmulc(D[0], D[2]), (R)0.5));
+    m12 = cadd(m12, cscale(cmulc(D[1], D[2]), (R)0.5));
+    const C v0 = p[(0 * 6 + q) * stride], v1 = p[(1 * 6 + q) * stride], v2 = p[(2 * 6 + q) * stride];
+    const C s3 = cscale(p[(3 * 6 + q) * stride], is2), s4 = cscale(p[(4 * 6 + q) * stride], is2),
+            s5 = cscale(p[(5 * 6 + q) * stride], is2);
+    b0 = cadd(b0, cadd(cmulc(v0, D[0]), cadd(cmulc(s4, D[2]), cmulc(s5, D[1]))));
+    b1 = cadd(b1, cadd(cmulc(v1, D[1]), cadd(cmulc(s3, D[2]), cmulc(s5, D[0]))));
+    b2 = cadd(b2, cadd(cmulc(v2, D[2]), cadd(cmulc(s3, D[1]), cmulc(s4, D[0]))));
+  }
+  // a = M^-1 b through the adjugate (M Hermitian: i10 = conj(i01), ...)
+  const R i00 = m11 * m22 - (m12.x * m12.x + m12.y * m12.y);
+  const R i11 = m00 * m22 - (m02.x * m02.x + m02.y * m02.y);
+  const R i22 = m00 * m11 - (m01.x * m01.x + m01.y * m01.y);
+  const C i01 = csub(cmulc(m02, m12), cscale(m01, m22));  // m02 conj(m12) - m01 m22
+  const C i02 = csub(cmul(m01, m12), cscale(m02, m11));   // m01 m12 - m02 m11
+  const C i12 = csub(cmulc(m02, m01), cscale(m12, m00));  // m02 conj(m01) - m00 m12
+  const R det = m00 * i00 + (m01.x * i01.x + m01.y * i01.y) + (m02.x * i02.x + m02.y * i02.y);
+  const R inv = (R)1 / det;
+  C a[3];
+  a[0] = cscale(cadd(cscale(b0, i00), cadd(cmul(i01, b1), cmul(i02, b2))), inv);
+  a[1] = cscale(cadd(cmulc(b0, i01), cadd(cscale(b1, i11), cmul(i12, b2))), inv);
+  a[2] = cscale(cadd(cmulc(b0, i02), cadd(cmulc(b1, i12), cscale(b2, i22))), inv);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    C D[3];
+    symbol(q, D);
+    p[(0 * 6 + q) * stride] = cmul(D[0], a[0]);
+    p[(1 * 6 + q) * stride] = cmul(D[1], a[1]);
+    p[(2 * 6 + q) * stride] = cmul(D[2], a[2]);
+    p[(3 * 6 + q) * stride] = cscale(cadd(cmul(D[1], a[2]), cmul(D[2], a[1])), is2);
+    p[(4 * 6 + q) * stride] = cscale(cadd(cmul(D[0], a[2]), cmul(D[2], a[0])), is2);
+    p[(5 * 6 + q) * stride] = cscale(cadd(cmul(D[0], a[1]), cmul(D[1], a[0])), is2);
+  }
+}
+
 }  // namespace rve

@@ -186,7 +186,9 @@ rve_status create_impl(rve_ctx* c, const uint8_t* phase_ids, const rve_phase* ph
   }
   CK(spectral_setup<R>(c->gs, m->sw), "spectral setup");
   m->sw.timer = &c->timer;
-  m->sw.generic = c->opts.passes == 1;
+  // the compiled passes carry up to six lines per voxel: the 36 of the
+  // Kuhn tetrahedra run on the generic passes
+  m->sw.generic = c->opts.passes == 1 || c->gs.ncomp > 6;
   m->sw.unfused = c->opts.passes == 2;
   const size_t nf = (size_t)g.ncomp * g.nvox * sizeof(R);
   const size_t ns = (size_t)g.nvox * sizeof(R);
@@ -895,10 +897,6 @@ rve_status rve_create(const int dims[3], int ndim, const uint8_t* phase_ids_dev,
     delete c;
     return fail(nullptr, RVE_ERR_ARG, "element must be 0 (one element per voxel) or 1 (Kuhn simplices)");
   }
-  if (c->opts.element == 1 && ndim != 2) {
-    delete c;
-    return fail(nullptr, RVE_ERR_ARG, "element 1 (Kuhn simplices) is built for 2D grids only");
-  }
   if (c->opts.element == 1 && c->opts.hessian != 0) {
     delete c;
     return fail(nullptr, RVE_ERR_ARG, "element 1 (Kuhn simplices) takes the secant Hessian only");
@@ -920,12 +918,27 @@ rve_status rve_create(const int dims[3], int ndim, const uint8_t* phase_ids_dev,
   g.nrows = (long long)g.ny * g.nz;
   c->gs = g;
   if (c->opts.element == 1) {
-    // 2D Kuhn triangles: two strain points per pixel; the spectral passes
-    // transform the six lines c * 2 + q of every pixel
-    c->gs.nq = 2;
-    c->gs.ncomp = 6;
-    g.nq = 2;
-    g.nvox = 2 * c->gs.nvox;
+    // Kuhn simplices: 2 triangles per pixel / 6 tetrahedra per voxel, one
+    // strain point each; the spectral passes transform the lines c * nq + q
+    // of every voxel (6 in 2D, 36 in 3D)
+    const int nq = ndim == 3 ? 6 : 2;
+    c->gs.nq = nq;
+    c->gs.ncomp = g.ncomp * nq;
+    g.nq = nq;
+    g.nvox = nq * c->gs.nvox;
+    if (ndim == 3) {
+      // the generic passes hold a tile of 36 lines: the x passes one row
+      // (18 packed line pairs of nx points within 16 per thread), the z
+      // pass one column (36 lines of nz points within 24 per thread and the
+      // shared-memory cap)
+      const size_t csz = (c->opts.precision == 32 ? 8 : 16);
+      if (18LL * g.nx > 256LL * 16 || 36LL * g.nz > 512LL * 24 || 36LL * g.nz * csz > 100 * 1024) {
+        delete c;
+        return fail(nullptr, RVE_ERR_ARG,
+                    "element 1 in 3D takes nx <= 227 and nz <= 341 (FP32) / 177 (FP64): the 36 lines of a row or "
+                    "a column must fit one block");
+      }
+    }
   }
   cudaError_t e = cudaMallocHost(&c->Sh, sizeof(DevScalars));
   if (e != cudaSuccess) {

@@ -61,8 +61,9 @@ class RVESolver:
         self._ids = ids
         self.phases = [p if isinstance(p, Phase) else Phase(*p) for p in phases]
         self.opts = make_opts(precision, **opts)
-        # strain points per voxel: 2 with the Kuhn-triangle element (2D)
-        self.nq = 2 if self.opts.element == 1 else 1
+        # strain points per voxel with the Kuhn-simplex element: 2 triangles
+        # (2D), 6 tetrahedra (3D)
+        self.nq = (6 if self.ndim == 3 else 2) if self.opts.element == 1 else 1
         self.fshape = ((self.ncomp, self.nq) if self.nq > 1 else (self.ncomp,)) + self.shape
         self.sshape = ((self.nq,) if self.nq > 1 else ()) + self.shape
         self._in()

@@ -110,6 +110,9 @@ def _args():
     p.add_argument("--probe", choices=["step", "fno"], default=None,
                    help="untimed small case for profilers: 'step' = one load step of a 256x256x128 sphere cell, "
                         "'fno' = three training iterations of the spectral neural operator at 64^3, batch 4")
+    p.add_argument("--passes", type=int, default=0, choices=[0, 1, 2, 3],
+                   help="rve_solver_opts.passes of the timed solver: 0 compiled five passes (default), 3 compiled "
+                        "with the cluster x+y passes, 2 unfused CG, 1 generic")
     p.add_argument("--probe-dims", default="256,256,128",
                    help="probe step: grid (nx,ny,nz); 256,128,256 gives the length-256 z pass the benchmark runs")
     p.add_argument("--batch-max-nr", type=int, default=50,
@@ -372,13 +375,13 @@ def run_gpu(args):
         R0 = 10.0 * (nvox ** 0.5) * ASR_STEP
         with torch.cuda.stream(st):
             s = RVESolver(dims, pm, ASR_PHASES, precision=32, stream=st, eta_eq=1e-6, eta_cg=1e-2, max_nr=400,
-                          R0=R0, Rmax=R0)
+                          R0=R0, Rmax=R0, passes=args.passes)
         s.set_eigenstrain([[0.0] * 6, [0.0] * 6, [-ASR_STEP] * 3 + [0.0] * 3])
         dE, free, workload = [0.0] * 6, [1] * 6, ASR_WORKLOAD
     else:
         with torch.cuda.stream(st):
             s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, stream=st, eta_eq=1e-6, eta_cg=1e-2,
-                          max_nr=400)
+                          max_nr=400, passes=args.passes)
         dE, free, workload = [0.0, 0.0, INC, 0.0, 0.0, 0.0], FREE, WORKLOAD
     eps0 = s.field(0.0)  # reference state: the unloaded cell
 
@@ -483,7 +486,7 @@ def run_gpu(args):
     # Newton iterations and not the product dominate: both Hessians
     onset = None
     if rank == 0 and not asr and not args.no_onset:
-        onset, _ = _onset_measure(n, 1, 1, st)
+        onset, _ = _onset_measure(n, 1, 1, st, args.passes)
         onset = {"workload": ONSET_WORKLOAD, **onset}
 
     if rank != 0:
@@ -512,6 +515,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload, "grid": [n, n, n], "parallelism": f"replicas x{ws}",
+                   "passes": args.passes,
                    "l2": "inputs larger than L2 (each 6-component FP32 field is 403 MB > 129 MB L2)",
                    "hv_per_step": hv / args.steps,
                    "nr_iters_per_step": [r["nr_iters"] for r in timed],
@@ -530,8 +534,11 @@ def run_gpu(args):
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_launch},
         "hv_roofline": {"bound": "hbm", "passes": hv_passes,
-                        "what": "one CG iteration's product: the five passes with the Steihaug iterate / residual "
-                                "update fused into the x-inverse (its reads of z, r, d and writes of z, r counted)",
+                        "what": "one CG iteration's product: the passes that launched -- the five separate passes "
+                                "(default), or with --passes 3 the x+y forward cluster pass (as x_fwd), the z pass "
+                                "and the y+x inverse cluster pass (as x_inv) -- with the Steihaug iterate / "
+                                "residual update of the inverse x pass (its reads of z, r, d and writes of z, r) "
+                                "counted",
                         "achieved": hv_bytes / (hv_only_ms / nprod / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": hv_bytes / (hv_only_ms / nprod / 1e3) / 1e9 / peak,
                         "algorithmic_bytes_per_product": hv_bytes,
@@ -802,7 +809,7 @@ ONSET_WORKLOAD = ("random-sphere cells (48 spheres at 128^3, 144 at 256^3, r~U[4
                   "symmetric consistent tangent")
 
 
-def _onset_measure(n, steps, warmup, st):
+def _onset_measure(n, steps, warmup, st, passes=0):
     """One load step at the damage onset of the n^3 sphere cell (48 spheres
     at 128^3, 144 at 256^3), timed with the secant and with the symmetric
     consistent Hessian from the same converged first increment."""
@@ -817,7 +824,7 @@ def _onset_measure(n, steps, warmup, st):
     for name, h in (("secant", 0), ("consistent", 1)):
         with torch.cuda.stream(st):
             s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, stream=st, eta_eq=1e-6, eta_cg=1e-2,
-                          max_nr=2000, R0=R0, Rmax=R0, hessian=h)
+                          max_nr=2000, R0=R0, Rmax=R0, hessian=h, passes=passes)
         first = s.solve_step(dE1, free_mask=FREE, raise_on_error=False)
         ref = s.get_state()
         eps0, kap0 = ref["eps"].clone(), ref["kappa"].clone()
@@ -870,7 +877,7 @@ def run_onset(args):
     st = torch.cuda.Stream()
     sizes, launches = {}, 0
     for n in [int(x) for x in args.onset_sizes.split(",")]:
-        sizes[str(n)], nl = _onset_measure(n, args.steps, args.warmup, st)
+        sizes[str(n)], nl = _onset_measure(n, args.steps, args.warmup, st, args.passes)
         launches += nl
     first = sizes[sorted(sizes, key=int)[0]]
     line = {
@@ -1031,7 +1038,8 @@ def run_probe(args):
         from synth import random_spheres
         dims = tuple(int(x) for x in args.probe_dims.split(","))
         pm = random_spheres(dims, count=100, rmin=4, rmax=10, seed=0)
-        s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, eta_eq=1e-6, eta_cg=1e-2, max_nr=50)
+        s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, eta_eq=1e-6, eta_cg=1e-2, max_nr=50,
+                      passes=args.passes)
         # the CG iterations stepped from the host: the same kernels, each a
         # separate launch a profiler can take (the device loop's are graph nodes)
         binding.rve_set_device_loop(s.h, False)

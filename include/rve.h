@@ -103,7 +103,13 @@ typedef struct {
                          implementation, for cross-checks); 2: the compiled
                          passes with the CG scalars and updates of the
                          generic path (d.Hd from the stored product, separate
-                         update kernels).  FP64 fields and other lengths
+                         update kernels); 3: as 0, and on 3D grids with
+                         Nx = Ny in {64, 96, 128, 192, 256} the x and y
+                         transforms of each direction in one pass (clusters
+                         of four CTAs sharing a z-plane's component through
+                         distributed shared memory; three passes per
+                         product, correct but slower than the five of 0 on
+                         this hardware).  FP64 fields and other lengths
                          always use the generic passes. */
   int element;        /* finite-element gradient the projection is built from
                          (Sec. 2.1, Eq. (9)): 0: one bilinear / trilinear

@@ -12,6 +12,7 @@
 
 #include <type_traits>
 
+#include "hv_cluster.cuh"
 #include "hv_fast.cuh"
 #include "hv_passes.cuh"
 #include "passes_generic.cuh"
@@ -96,6 +97,17 @@ cudaError_t spectral_setup(const GridDesc& g, SpecWork<R>& w) {
     if ((e = upload_tables<R>(ns[a], &w.tw[a], &w.gdiff[a], &w.gavg[a])) != cudaSuccess) return e;
   const size_t nspec = (size_t)g.ncomp * g.nrows * g.nxh;
   if ((e = cudaMalloc(&w.spec, nspec * sizeof(C))) != cudaSuccess) return e;
+  if (std::is_same<R, float>::value && cluster_size_ok(g)) {
+    // twiddles of the cluster passes' M-point y sub-transform (M = Nx / 4)
+    const int m = g.nx / 4;
+    std::vector<C> t(m);
+    for (int k = 0; k < m; ++k) {
+      const long double th = 2.0L * 3.14159265358979323846264338327950288L * (long double)k / (long double)m;
+      t[k] = C{(R)cosl(th), (R)(-sinl(th))};
+    }
+    if ((e = cudaMalloc(&w.twq, m * sizeof(C))) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(w.twq, t.data(), m * sizeof(C), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  }
   // x passes: npair * nx <= kXThreads * kXEpt complex per block
   const int ex = kXThreads * kXEpt;
   int q = (2 * ex) / (g.ncomp * g.nx);
@@ -170,14 +182,17 @@ void spectral_free(SpecWork<R>& w) {
   }
   if (w.spec) cudaFree(w.spec);
   if (w.partials) cudaFree(w.partials);
+  if (w.twq) cudaFree(w.twq);
   w.spec = nullptr;
   w.partials = nullptr;
+  w.twq = nullptr;
 }
 
 // y / z passes with the projection (3D) or the y pass with the projection
 // (2D), between the x-forward and the x-inverse passes.
 template <typename R>
-static cudaError_t spectral_middle(const GridDesc& g, SpecWork<R>& w, cudaStream_t st, long long* nlp) {
+static cudaError_t spectral_middle(const GridDesc& g, SpecWork<R>& w, cudaStream_t st, long long* nlp,
+                                   bool skip_yfwd = false, bool skip_yinv = false) {
   using C = Cx<R>;
   constexpr bool F32 = std::is_same<R, float>::value;
   long long nl = 0;
@@ -188,6 +203,7 @@ static cudaError_t spectral_middle(const GridDesc& g, SpecWork<R>& w, cudaStream
     const dim3 zg((g.nxh + w.tz - 1) / w.tz, g.ny);
     const size_t zsm = (size_t)g.ncomp * w.tz * g.nz * sizeof(C);
     for (int pass = 0; pass < 3; ++pass) {
+      if ((pass == 0 && skip_yfwd) || (pass == 2 && skip_yinv)) continue;  // done by the cluster x+y passes
       e = cudaErrorNotSupported;
       PassScope ps(w.timer, st, pass == 0 ? PASS_YFWD : (pass == 1 ? PASS_ZPROJ : PASS_YINV));
       if constexpr (F32) {
@@ -225,6 +241,13 @@ static cudaError_t spectral_middle(const GridDesc& g, SpecWork<R>& w, cudaStream
   return cudaSuccess;
 }
 
+// the cluster x+y passes were asked for and apply (3D FP32, Nx = Ny of a
+// cluster length)
+template <typename R>
+static bool use_cluster(const GridDesc& g, const SpecWork<R>& w) {
+  return std::is_same<R, float>::value && w.cluster && !w.generic && w.twq != nullptr && cluster_size_ok(g);
+}
+
 template <typename R>
 cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>& mt, const R* in,
                            const uint8_t* phase, const R* damage, XIn mode, R* out,
@@ -240,12 +263,22 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
   // tangent it already computes, so the x-inverse need not read `in` again
   bool fwd_dot = false;
   int fwd_blocks = 0;
+  // the cluster passes take the x and y transforms together (not the
+  // consistent tangent's forward pass)
+  const bool cl = use_cluster(g, w);
+  const bool cl_fwd = cl && !(mode == XIn::Tangent && w.cons.dp != nullptr);
   // x forward (tangent fused)
   e = cudaErrorNotSupported;
   {
   PassScope ps(w.timer, st, PASS_XFWD);
   if constexpr (F32) {
-    if (!w.generic && fast_size(g.nx)) {
+    if (cl_fwd) {
+      const bool want = mode == XIn::Tangent && dot_with != nullptr && dot_with == in && !w.unfused;
+      e = cluster_xyfwd(g, in, phase, damage, mt, w.spec, w.tw[0], w.twq, mode == XIn::Tangent,
+                        want ? w.partials : nullptr, st);
+      fwd_blocks = cluster_blocks(g);
+      fwd_dot = want && e == cudaSuccess;
+    } else if (!w.generic && fast_size(g.nx)) {
       const bool want = mode == XIn::Tangent && dot_with != nullptr && dot_with == in && !w.unfused;
       e = fast_xfwd(g, in, phase, damage, mt, w.spec, w.tw[0], mode == XIn::Tangent, want ? w.partials : nullptr,
                     &fwd_blocks, st, &w.cons);
@@ -263,7 +296,7 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
   }
   if (e != cudaSuccess) return e;
   ++nl;
-  if ((e = spectral_middle<R>(g, w, st, &nl)) != cudaSuccess) return e;
+  if ((e = spectral_middle<R>(g, w, st, &nl, cl_fwd, cl)) != cudaSuccess) return e;
   const R scale = (R)(1.0 / (double)g.nvox);
   const bool dot = dot_with != nullptr && !fwd_dot;
   const bool self = dot && (dot_with == out);
@@ -272,8 +305,12 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
   {
   PassScope ps(w.timer, st, PASS_XINV);
   if constexpr (F32) {
-    if (!w.generic && fast_size(g.nx))
+    if (cl) {
+      e = cluster_yxinv(g, w.spec, out, self ? nullptr : dot_with, w.partials, w.tw[0], w.twq, dot, self, st);
+      nblocks = cluster_blocks(g);
+    } else if (!w.generic && fast_size(g.nx)) {
       e = fast_xinv(g, w.spec, out, self ? nullptr : dot_with, w.partials, w.tw[0], dot, self, &nblocks, st);
+    }
   }
   if (e == cudaErrorNotSupported) {
     nblocks = xblocks;
@@ -304,18 +341,29 @@ cudaError_t spectral_hv_cg(const GridDesc& g, SpecWork<float>& w, const MatTable
   long long nl = 0;
   cudaError_t e;
   int fb = 0, ib = 0;
+  const bool cl = use_cluster(g, w), cl_fwd = cl && w.cons.dp == nullptr;
   {
     PassScope ps(w.timer, st, PASS_XFWD);
-    e = fast_xfwd(g, d, phase, damage, mt, w.spec, w.tw[0], true, w.partials, &fb, st, &w.cons);
+    if (cl_fwd) {
+      e = cluster_xyfwd(g, d, phase, damage, mt, w.spec, w.tw[0], w.twq, true, w.partials, st);
+      fb = cluster_blocks(g);
+    } else {
+      e = fast_xfwd(g, d, phase, damage, mt, w.spec, w.tw[0], true, w.partials, &fb, st, &w.cons);
+    }
   }
   if (e != cudaSuccess) return e;
   ++nl;
   if ((e = reduce_partials(w.partials, fb, 1, dHd, st, &nl)) != cudaSuccess) return e;
-  if ((e = spectral_middle<float>(g, w, st, &nl)) != cudaSuccess) return e;
+  if ((e = spectral_middle<float>(g, w, st, &nl, cl_fwd, cl)) != cudaSuccess) return e;
   if ((e = between(between_arg)) != cudaSuccess) return e;
   {
     PassScope ps(w.timer, st, PASS_XINV);
-    e = fast_xinv_cg(g, w.spec, z, r, d, status, alpha, tau, w.partials, w.tw[0], &ib, st);
+    if (cl) {
+      e = cluster_yxinv_cg(g, w.spec, z, r, d, status, alpha, tau, w.partials, w.tw[0], w.twq, st);
+      ib = cluster_blocks(g);
+    } else {
+      e = fast_xinv_cg(g, w.spec, z, r, d, status, alpha, tau, w.partials, w.tw[0], &ib, st);
+    }
   }
   if (e != cudaSuccess) return e;
   ++nl;

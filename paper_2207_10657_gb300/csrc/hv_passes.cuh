@@ -13,8 +13,9 @@ struct GridDesc {
   int ncomp;      // 3 or 6
   long long nvox;
   long long nrows;  // ny * nz voxel rows along x
-  int nq = 1;       // strain points per voxel: 1 (one element per voxel) or 2 (2D Kuhn
-                    // triangles; the spectral lines are then c * 2 + q, ncomp = 6)
+  int nq = 1;       // strain points per voxel: 1 (one element per voxel), 2 (2D Kuhn
+                    // triangles) or 6 (3D Kuhn tetrahedra); the spectral lines are then
+                    // c * nq + q, ncomp = 6 or 36
 };
 
 // Rank-one part of the symmetric consistent damage tangent, per voxel: the
@@ -45,6 +46,8 @@ template <typename R> struct SpecWork {
   ConsTan<R> cons;             // set: tangent passes apply the consistent tangent
   bool generic = false;        // true: never take the compiled FP32 passes
   bool unfused = false;        // true: compiled passes, but CG scalars and updates as the generic path
+  bool cluster = false;        // true: the cluster x+y passes where they apply (opt-in: slower, see hv_cluster.cu)
+  Cx<R>* twq = nullptr;        // e^{-2 pi i t / (Nx/4)}: the cluster passes' y sub-transform
 };
 
 enum class XIn { Plain = 0, Tangent = 1 };

@@ -190,6 +190,7 @@ rve_status create_impl(rve_ctx* c, const uint8_t* phase_ids, const rve_phase* ph
   // Kuhn tetrahedra run on the generic passes
   m->sw.generic = c->opts.passes == 1 || c->gs.ncomp > 6;
   m->sw.unfused = c->opts.passes == 2;
+  m->sw.cluster = c->opts.passes == 3;
   const size_t nf = (size_t)g.ncomp * g.nvox * sizeof(R);
   const size_t ns = (size_t)g.nvox * sizeof(R);
   R** fields[] = {&m->eps, &m->sig, &m->sig_t, &m->g, &m->z, &m->r, &m->d, &m->Hd, &m->tmp};
@@ -901,9 +902,11 @@ rve_status rve_create(const int dims[3], int ndim, const uint8_t* phase_ids_dev,
     delete c;
     return fail(nullptr, RVE_ERR_ARG, "element 1 (Kuhn simplices) takes the secant Hessian only");
   }
-  if (c->opts.passes < 0 || c->opts.passes > 2) {
+  if (c->opts.passes < 0 || c->opts.passes > 3) {
     delete c;
-    return fail(nullptr, RVE_ERR_ARG, "passes must be 0 (compiled, fused CG), 1 (generic) or 2 (compiled, unfused CG)");
+    return fail(nullptr, RVE_ERR_ARG,
+                "passes must be 0 (compiled, fused CG), 1 (generic), 2 (compiled, unfused CG) or 3 (compiled, "
+                "fused CG, cluster x+y passes)");
   }
   c->precision = c->opts.precision;
   c->st = static_cast<cudaStream_t>(stream);

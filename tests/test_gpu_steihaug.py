@@ -3,8 +3,12 @@ oracle's steihaug_cg on the same Hessian and gradient (needs a GB300).
 
 The cases run on axis length 32, where the compiled FP32 passes and the CG
 update fused into the x-inverse pass are used (passes = 0), through the
-compiled passes with separate CG update kernels (passes = 2) and through the
-generic passes (passes = 1); FP64 fields use the generic passes.  The state
+compiled passes with separate CG update kernels (passes = 2), through the
+generic passes (passes = 1) and with the cluster x+y passes (passes = 3);
+FP64 fields use the generic passes.  On the 64 x 64 x 16 cell passes = 3
+takes the cluster passes (x and y transforms of each direction in one pass,
+the CG update fused into the inverse one; the consistent tangent's forward
+stays on the separate x and y passes); on 32^3 it equals passes = 0.  The state
 holds a fully damaged band (kappa_n >= kappa_f, D = 1) and a matrix loaded
 into softening, and the radius / Hessian are chosen so that every exit of
 Algorithm 1 is taken: the boundary (positive root of |z + tau d| = R), the
@@ -71,6 +75,11 @@ CASES = [
     ((32, 32, 32), 0, 1.0, "converged"),
     ((32, 32, 32), 1, 0.05, "boundary"),
     ((32, 32, 32), 1, 10.0, "negative_curvature"),
+    # Nx = Ny = 64: with passes = 3 the x and y transforms in one cluster pass per direction
+    ((64, 64, 16), 0, 0.05, "boundary"),
+    ((64, 64, 16), 0, 1.0, "converged"),
+    ((64, 64, 16), 1, 0.05, "boundary"),
+    ((64, 64, 16), 1, 10.0, "negative_curvature"),
 ]
 
 
@@ -85,7 +94,7 @@ def _oracle_solve(dims, hessian, R):
     return z, info
 
 
-@pytest.mark.parametrize("precision,passes", [(32, 0), (32, 1), (32, 2), (64, 0)])
+@pytest.mark.parametrize("precision,passes", [(32, 0), (32, 1), (32, 2), (32, 3), (64, 0)])
 @pytest.mark.parametrize("dims,hessian,R,reason", CASES)
 def test_steihaug_exit_matches_oracle(dims, hessian, R, reason, precision, passes):
     from paper_2207_10657_gb300 import RVESolver, build

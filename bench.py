@@ -113,6 +113,10 @@ def _args():
     p.add_argument("--passes", type=int, default=0, choices=[0, 1, 2, 3],
                    help="rve_solver_opts.passes of the timed solver: 0 compiled five passes (default), 3 compiled "
                         "with the cluster x+y passes, 2 unfused CG, 1 generic")
+    p.add_argument("--host-loop", action="store_true",
+                   help="step the Steihaug-CG iterations from the host in every timed step (the same kernels as "
+                        "the device-side graph loop, each a separate launch; for profilers, which do not take "
+                        "the kernels inside conditional graph nodes)")
     p.add_argument("--probe-dims", default="256,256,128",
                    help="probe step: grid (nx,ny,nz); 256,128,256 gives the length-256 z pass the benchmark runs")
     p.add_argument("--batch-max-nr", type=int, default=50,
@@ -383,6 +387,8 @@ def run_gpu(args):
             s = RVESolver(dims, pm, [MATRIX, STIFF], precision=32, stream=st, eta_eq=1e-6, eta_cg=1e-2,
                           max_nr=400, passes=args.passes)
         dE, free, workload = [0.0, 0.0, INC, 0.0, 0.0, 0.0], FREE, WORKLOAD
+    if args.host_loop:
+        binding.rve_set_device_loop(s.h, False)
     eps0 = s.field(0.0)  # reference state: the unloaded cell
 
     def step():
@@ -515,7 +521,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload, "grid": [n, n, n], "parallelism": f"replicas x{ws}",
-                   "passes": args.passes,
+                   "passes": args.passes, "host_loop": bool(args.host_loop),
                    "l2": "inputs larger than L2 (each 6-component FP32 field is 403 MB > 129 MB L2)",
                    "hv_per_step": hv / args.steps,
                    "nr_iters_per_step": [r["nr_iters"] for r in timed],

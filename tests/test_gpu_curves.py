@@ -17,6 +17,11 @@ paths (needs a GB300).
   voxels within 1e-3 of kappa0), up to the first increment the oracle does
   not converge within 400 Newton iterations (a snap-back); that increment
   is run on the GPU too and its outcome printed (pytest -s).
+* The third configuration's mixed path (eps_zz and eps_yz ramped together,
+  the other four components stress-free) on its sphere model (three times
+  the spheres) at 32^3 against tests/golden/make_config3_32.py's stored
+  oracle path in the same way, with both stressed components (zz, yz)
+  compared per increment.
 """
 import json
 import os
@@ -35,6 +40,7 @@ torch = pytest.importorskip("torch")
 MATRIX = (1.0, 0.3, True, 1e-4, 1e-3)
 STIFF = (10.0, 0.2, False, 0.0, 0.0)
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config2_32.json")
+GOLDEN3 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config3_32.json")
 
 
 def _solver(dims, pm, precision, **kw):
@@ -101,6 +107,45 @@ def test_config2_path_32cube_matches_stored_oracle(precision, hessian):
         damaged = len(rec["damaged"]) > 0
         rel = abs(sg[2] - so[2]) / scale
         assert rel < (1e-4 if damaged else 1e-5), (rec["n"], rel)
+        st = s.get_state()
+        eps = st["eps"].cpu().numpy().astype(np.float64).reshape(6, -1)[:, sample]
+        eref = np.array(rec["strain_sample"])
+        assert np.linalg.norm(eps - eref) / np.linalg.norm(eref) < 1e-4
+        kap = st["kappa"].cpu().numpy().astype(np.float64).ravel()
+        near = np.zeros(kap.size, bool)
+        near[rec["near_threshold"]] = True
+        got = np.flatnonzero((kap > K0) & ~near)
+        assert np.array_equal(got, np.array(rec["damaged"], dtype=got.dtype)), (rec["n"], got.size, len(rec["damaged"]))
+    s.close()
+
+
+@pytest.mark.parametrize("precision,hessian", [(32, 0), (64, 1)])
+def test_config3_mixed_path_32cube_matches_stored_oracle(precision, hessian):
+    import sys
+    sys.path.insert(0, os.path.dirname(GOLDEN3))
+    from make_config3_32 import cell, INC, K0
+    with open(GOLDEN3) as f:
+        ref = json.load(f)
+    pm = cell()
+    R0 = ref["R0"]
+    eta = 1e-6 if precision == 32 else 1e-8
+    s = _solver((32, 32, 32), pm, precision, R0=R0, Rmax=R0, eta_eq=eta, eta_cg=1e-2, max_nr=400,
+                max_cg=1000, hessian=hessian)
+    sample = np.array(ref["sample_points"])
+    print(f"\nFP{precision} hessian={hessian}: increment, oracle (sigma_zz, sigma_yz), GPU, Newton (oracle, GPU)")
+    scale = np.zeros(2)
+    for rec in ref["increments"]:
+        rep = s.solve_step(list(INC), free_mask=ref["free_mask"], raise_on_error=False)
+        so, sg = np.array(rec["mean_stress"])[[2, 3]], np.array(rep["mean_stress"])[[2, 3]]
+        print(f"  {rec['n']}  {so}  {sg}  ({rec['nr_iters']}, {rep['nr_iters']}) "
+              f"converged ({rec['converged']}, {rep['converged']})")
+        if not rec["converged"]:
+            break  # the oracle's snap-back: no reference for this increment
+        assert rep["converged"]
+        scale = np.maximum(scale, np.abs(so))
+        damaged = len(rec["damaged"]) > 0
+        rel = np.abs(sg - so) / scale
+        assert np.all(rel < (1e-4 if damaged else 1e-5)), (rec["n"], rel)
         st = s.get_state()
         eps = st["eps"].cpu().numpy().astype(np.float64).reshape(6, -1)[:, sample]
         eref = np.array(rec["strain_sample"])

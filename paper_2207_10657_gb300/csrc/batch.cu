@@ -121,7 +121,7 @@ __global__ void kb_compact(WLists* wl, const int* __restrict__ nb, int n, Gate g
 // XMODE: 0 plain x-forward, 1 tangent x-forward.  YINV: y direction.
 // DOT for the x-inverse: 0 none, 1 with dotw, 2 self.
 template <int XMODE>
-__global__ void __launch_bounds__(kXThreads)
+__global__ void __launch_bounds__(kXThreads, kXYMinBlocks)
     kb_xfwd(const BDesc* __restrict__ D, const WLists* __restrict__ wl, int* counter,
             const DevScalars* __restrict__ S, const MatTable<R> mt, const R* __restrict__ in,
             const uint8_t* __restrict__ phase, const R* __restrict__ dmg) {
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kXThreads)
 }
 
 template <bool YINV>
-__global__ void __launch_bounds__(kYThreads)
+__global__ void __launch_bounds__(kYThreads, kXYMinBlocks)
     kb_ycols(const BDesc* __restrict__ D, const WLists* __restrict__ wl, int* counter) {
   __shared__ int s_item;
   for (;;) {
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kZThreads)
   }
 }
 
-__global__ void __launch_bounds__(kYThreads)
+__global__ void __launch_bounds__(kYThreads, kXYMinBlocks)
     kb_yproj2d(const BDesc* __restrict__ D, const WLists* __restrict__ wl, int* counter) {
   __shared__ int s_item;
   for (;;) {
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kYThreads)
 }
 
 template <int DOT>
-__global__ void __launch_bounds__(kXThreads)
+__global__ void __launch_bounds__(kXThreads, kXYMinBlocks)
     kb_xinv(const BDesc* __restrict__ D, const WLists* __restrict__ wl, int* counter,
             const DevScalars* __restrict__ S, R* __restrict__ out, const R* __restrict__ dotw,
             double* __restrict__ partials) {
@@ -541,41 +541,41 @@ cudaError_t batch_apply(rve_batch_ctx* c, const R* in, R* out, bool tangent, con
   {
     const int tot = c->total[BP_X];
     if (tangent)
-      kb_xfwd<1><<<grid_for(tot, 4), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
+      kb_xfwd<1><<<grid_for(tot, kXYMinBlocks), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
                                                                         next_counter(c), c->S, c->mt, in,
                                                                         c->phase, c->D);
     else
-      kb_xfwd<0><<<grid_for(tot, 4), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
+      kb_xfwd<0><<<grid_for(tot, kXYMinBlocks), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
                                                                         next_counter(c), c->S, c->mt, in,
                                                                         c->phase, c->D);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (c->any3d) {
-    kb_ycols<false><<<grid_for(c->total[BP_Y], 4), kYThreads, c->smem[BP_Y], c->st>>>(
+    kb_ycols<false><<<grid_for(c->total[BP_Y], kXYMinBlocks), kYThreads, c->smem[BP_Y], c->st>>>(
         c->dD, c->wl, next_counter(c));
     kb_zproj<<<grid_for(c->total[BP_Z], 2), kZThreads, c->smem[BP_Z], c->st>>>(c->dD, c->wl, next_counter(c));
-    kb_ycols<true><<<grid_for(c->total[BP_Y], 4), kYThreads, c->smem[BP_Y], c->st>>>(
+    kb_ycols<true><<<grid_for(c->total[BP_Y], kXYMinBlocks), kYThreads, c->smem[BP_Y], c->st>>>(
         c->dD, c->wl, next_counter(c));
     c->launches += 3;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (c->any2d) {
-    kb_yproj2d<<<grid_for(c->total[BP_2D], 4), kYThreads, c->smem[BP_2D], c->st>>>(
+    kb_yproj2d<<<grid_for(c->total[BP_2D], kXYMinBlocks), kYThreads, c->smem[BP_2D], c->st>>>(
         c->dD, c->wl, next_counter(c));
     ++c->launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const int tot = c->total[BP_X];
   if (!dotw) {
-    kb_xinv<0><<<grid_for(tot, 4), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
+    kb_xinv<0><<<grid_for(tot, kXYMinBlocks), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
                                                                       next_counter(c), c->S, out, nullptr,
                                                                       nullptr);
   } else if (dotw == out) {
-    kb_xinv<2><<<grid_for(tot, 4), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
+    kb_xinv<2><<<grid_for(tot, kXYMinBlocks), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
                                                                       next_counter(c), c->S, out, nullptr,
                                                                       c->part);
   } else {
-    kb_xinv<1><<<grid_for(tot, 4), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
+    kb_xinv<1><<<grid_for(tot, kXYMinBlocks), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
                                                                       next_counter(c), c->S, out, dotw,
                                                                       c->part);
   }

@@ -12,6 +12,12 @@ constexpr int kXThreads = 256, kXEpt = 16;  // x passes
 constexpr int kYThreads = 256, kYEpt = 16;  // y columns, 2D y+projection
 constexpr int kZThreads = 512, kZEpt = 24;  // z + projection
 constexpr int kSmemCap = 100 * 1024;        // dynamic shared memory cap per block
+// The x and y kernels are compiled for six resident blocks per SM (at most
+// 42 registers a thread): their runtime-radix stages otherwise take 200-255
+// registers and leave one block (8 warps) per SM, latency-bound.  The spills
+// this costs are cheaper than the idle SM (2.4x faster generic passes at
+// 256^3 FP32, 1.3x in FP64 at 128^3).
+constexpr int kXYMinBlocks = 6;
 
 // ------------------------------------------------------------ x forward
 // Q voxel rows per block, all ncomp components of each row.  With the
@@ -111,7 +117,7 @@ __device__ __forceinline__ void xfwd_body(const R* __restrict__ in, const uint8_
 }
 
 template <typename R, int MODE>
-__global__ void __launch_bounds__(kXThreads)
+__global__ void __launch_bounds__(kXThreads, kXYMinBlocks)
     k_xfwd(const R* __restrict__ in, const uint8_t* __restrict__ phase, const R* __restrict__ dmg,
            const MatTable<R> mt, Cx<R>* __restrict__ spec, const GridDesc g, const int Q, const AxisPlan px,
            const Cx<R>* __restrict__ tw, const ConsTan<R> ct) {
@@ -143,7 +149,7 @@ __device__ __forceinline__ void ycols_body(Cx<R>* __restrict__ spec, const GridD
 }
 
 template <typename R, bool INV>
-__global__ void __launch_bounds__(kYThreads)
+__global__ void __launch_bounds__(kYThreads, kXYMinBlocks)
     k_ycols(Cx<R>* __restrict__ spec, const GridDesc g, const int TX, const AxisPlan py,
             const Cx<R>* __restrict__ tw) {
   ycols_body<R, INV>(spec, g, TX, py, tw, blockIdx.x, blockIdx.y, blockIdx.z);
@@ -268,7 +274,7 @@ __device__ __forceinline__ void yproj2d_body(Cx<R>* __restrict__ spec, const Gri
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kYThreads)
+__global__ void __launch_bounds__(kYThreads, kXYMinBlocks)
     k_yproj2d(Cx<R>* __restrict__ spec, const GridDesc g, const int TX, const AxisPlan py,
               const Cx<R>* __restrict__ tw, const Cx<R>* __restrict__ gdx, const Cx<R>* __restrict__ gax,
               const Cx<R>* __restrict__ gdy, const Cx<R>* __restrict__ gay, const unsigned free_mask) {
@@ -335,7 +341,7 @@ __device__ __forceinline__ void xinv_body(const Cx<R>* __restrict__ spec, R* __r
 }
 
 template <typename R, bool DOT>
-__global__ void __launch_bounds__(kXThreads)
+__global__ void __launch_bounds__(kXThreads, kXYMinBlocks)
     k_xinv(const Cx<R>* __restrict__ spec, R* __restrict__ out, const R* __restrict__ dotw,
            double* __restrict__ partials, const GridDesc g, const int Q, const AxisPlan px,
            const Cx<R>* __restrict__ tw, const R scale, const bool self_dot) {

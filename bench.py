@@ -119,6 +119,11 @@ def _args():
                         "the kernels inside conditional graph nodes)")
     p.add_argument("--probe-dims", default="256,256,128",
                    help="probe step: grid (nx,ny,nz); 256,128,256 gives the length-256 z pass the benchmark runs")
+    p.add_argument("--batch-hessian", type=int, default=1, choices=[0, 1],
+                   help="batch96: Hessian of the batched solves (0 secant, 1 symmetric consistent tangent)")
+    p.add_argument("--batch-increments", type=int, default=0,
+                   help="batch96: after the timed step, run this many increments of the load path from the "
+                        "unloaded cells and report converged members per increment (the configuration's 30)")
     p.add_argument("--batch-max-nr", type=int, default=50,
                    help="Newton cap per member for batch96 (bounds the work of members that localise)")
     return p.parse_args()
@@ -610,7 +615,8 @@ def run_batch(args):
     free = [[0] * (3 if len(d) == 2 else 6) for d in dims]
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
-        b = RVEBatch(dims, pms, [MATRIX, STIFF], stream=st, eta_eq=1e-6, eta_cg=1e-2, max_nr=args.batch_max_nr)
+        b = RVEBatch(dims, pms, [MATRIX, STIFF], stream=st, eta_eq=1e-6, eta_cg=1e-2, max_nr=args.batch_max_nr,
+                     hessian=args.batch_hessian)
         tuned = b.autotune(reps=3)
 
     def step():
@@ -641,13 +647,29 @@ def run_batch(args):
     per_step = sum(r["hv_products"] * nv for r, nv in zip(reps, nvox))
     value = per_step * args.steps / (ms / 1e3)
     launches = b.launch_count - l0
+    path = None
+    if args.batch_increments > 0:
+        # the load path: increments accumulate from the unloaded cells
+        b.reset()
+        path = []
+        for k in range(args.batch_increments):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            rk = b.solve_step(dEs, free, raise_on_error=False)
+            e1.record(st)
+            torch.cuda.synchronize()
+            nr = [x["nr_iters"] for x in rk]
+            path.append({"increment": k + 1, "converged": sum(1 for x in rk if x["converged"]),
+                         "nr_mean": sum(nr) / len(nr), "nr_max": max(nr),
+                         "hv_mean": sum(x["hv_products"] for x in rk) / len(rk), "ms": e0.elapsed_time(e1)})
+            print(f"batch path increment {k + 1}: {path[-1]}", file=sys.stderr, flush=True)
     b.close()
     # the same members solved one after another with single-cell contexts
     singles = []
     with torch.cuda.stream(st):
         for d, pm in zip(dims, pms):
             singles.append(RVESolver(d, pm, [MATRIX, STIFF], precision=32, stream=st, eta_eq=1e-6, eta_cg=1e-2,
-                                     max_nr=args.batch_max_nr))
+                                     max_nr=args.batch_max_nr, hessian=args.batch_hessian))
     zero = [s.field(0.0) for s in singles]
     for s, z, de, fm in zip(singles, zero, dEs, free):
         s.set_state(z)
@@ -673,6 +695,8 @@ def run_batch(args):
                    "sequential_single_contexts_ms": t_single * 1e3,
                    "sequential_single_contexts_voxel_hv_per_s": hv_single / t_single,
                    "batched_speedup": (t_single * 1e3) / (ms / args.steps),
+                   "hessian": "consistent" if args.batch_hessian else "secant",
+                   "max_nr": args.batch_max_nr, "path": path,
                    "autotune": tuned},
         "gpu_launches": launches, "clocks": clocks,
     }

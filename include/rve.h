@@ -92,7 +92,11 @@ typedef struct {
                          Hessian-vector products and the model change of the
                          trust-region step; costs 4 B/voxel per product plus
                          C:eps and n on loading voxels, and 13 reals per voxel
-                         of storage.  The batched solver keeps the secant. */
+                         of storage.  The batched solver (rve_batch_create)
+                         takes 0 or 1 as well; with 1 it prepares the per-voxel
+                         data once per member and accepted state, and every
+                         batched tangent product (rve_batch_hessp too) uses
+                         the state's consistent tangent. */
   int passes;         /* 0: FP32 fields use the passes compiled for the axis
                          lengths 32, 64, 128, 256, 512, 96, 192 and 384
                          (per axis), with the Steihaug-CG iterate / residual

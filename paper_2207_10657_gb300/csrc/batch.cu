@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/rve.h"
+#include "consistent.cuh"
 #include "passes_generic.cuh"
 #include "scalar_logic.cuh"
 #include "solver_kernels.cuh"
@@ -120,18 +121,22 @@ __global__ void kb_compact(WLists* wl, const int* __restrict__ nb, int n, Gate g
 // ------------------------------------------------------ spectral passes
 // XMODE: 0 plain x-forward, 1 tangent x-forward.  YINV: y direction.
 // DOT for the x-inverse: 0 none, 1 with dotw, 2 self.
+// cdp, ca, cn (batched like the state, may be NULL): the rank-one part of
+// the symmetric consistent tangent (ConsTan), applied with XMODE 1.
 template <int XMODE>
 __global__ void __launch_bounds__(kXThreads, kXYMinBlocks)
     kb_xfwd(const BDesc* __restrict__ D, const WLists* __restrict__ wl, int* counter,
             const DevScalars* __restrict__ S, const MatTable<R> mt, const R* __restrict__ in,
-            const uint8_t* __restrict__ phase, const R* __restrict__ dmg) {
+            const uint8_t* __restrict__ phase, const R* __restrict__ dmg, const R* __restrict__ cdp,
+            const R* __restrict__ ca, const R* __restrict__ cn) {
   __shared__ int s_item;
   for (;;) {
     int v, i, lb;
     if (!fetch(wl, BP_X, counter, &s_item, &v, &i, &lb)) break;
     const BDesc& d = D[i];
+    const ConsTan<R> ct{cdp ? cdp + d.voff : nullptr, ca ? ca + d.foff : nullptr, cn ? cn + d.foff : nullptr};
     xfwd_body<R, XMODE>(in + d.foff, phase + d.voff, dmg + d.voff, mt, d.spec, d.g, d.qx, d.px, d.tw[0],
-                        lb);
+                        lb, ct);
   }
 }
 
@@ -314,7 +319,8 @@ __global__ void __launch_bounds__(256)
              const uint8_t* __restrict__ phase,
              const R* __restrict__ eps, const R* __restrict__ p, const R* __restrict__ khist,
              const R* __restrict__ sig0, const R* __restrict__ D0, R* __restrict__ sig_t, R* __restrict__ D_t,
-             R* __restrict__ kap_t, double* __restrict__ part) {
+             R* __restrict__ kap_t, double* __restrict__ part, const R* __restrict__ cdp = nullptr,
+             const R* __restrict__ ca = nullptr, const R* __restrict__ cn = nullptr) {
   __shared__ int s_item;
   constexpr int NS = MEANS ? 12 : 6;
   __shared__ double red[NS * 32];
@@ -357,10 +363,21 @@ __global__ void __launch_bounds__(256)
         trp += pv[q];
       }
       const R keep0 = D0 ? (R)1 - D0[d.voff + k] : (R)1;
+      // p:B0:p of the model with the Hessian of the state: the secant, plus
+      // the consistent tangent's rank-one part where cdp is set
+      const R hdp = (cdp && p) ? (R)0.5 * cdp[d.voff + k] : (R)0;
+      R np_ = 0, ap_ = 0;
+      if (hdp != (R)0) {
+        for (int c = 0; c < nc; ++c) {
+          np_ += cn[fo + c * nv] * pv[c];
+          ap_ += ca[fo + c * nv] * pv[c];
+        }
+      }
       for (int c = 0; c < nc; ++c) {
         const R sv = keep * ((R)2 * mu * e[c] + (c < nd ? lam * tr : (R)0));
         sig_t[fo + c * nv] = sv;
-        const R bp = keep0 * ((R)2 * mu * pv[c] + (c < nd ? lam * trp : (R)0));
+        R bp = keep0 * ((R)2 * mu * pv[c] + (c < nd ? lam * trp : (R)0));
+        if (hdp != (R)0) bp -= hdp * (ca[fo + c * nv] * np_ + cn[fo + c * nv] * ap_);
         if (sig0) acc[0].add(sig0[fo + c * nv] * pv[c]);
         acc[1].add(sv * pv[c]);
         acc[2].add(pv[c] * bp);
@@ -461,6 +478,9 @@ struct rve_batch_ctx {
   R *eps = nullptr, *sig = nullptr, *sig_t = nullptr, *gv = nullptr, *z = nullptr, *r = nullptr, *d = nullptr,
     *Hd = nullptr, *tmp = nullptr;
   R *D = nullptr, *D_t = nullptr, *kap = nullptr, *kap_t = nullptr, *khist = nullptr;
+  // symmetric consistent tangent (opts.hessian = 1): D'(kappa) per voxel, C:eps
+  // and eps^(t)/kappa per field element, refreshed for every accepted state
+  R *cdp = nullptr, *ca = nullptr, *cn = nullptr;
   uint8_t* phase = nullptr;
   DevScalars* S = nullptr;
   DevScalars* Sh = nullptr;
@@ -540,14 +560,17 @@ cudaError_t batch_apply(rve_batch_ctx* c, const R* in, R* out, bool tangent, con
   if ((e = compact(c, gt)) != cudaSuccess) return e;
   {
     const int tot = c->total[BP_X];
+    // hessian = 1: every tangent product carries the consistent tangent's
+    // rank-one part of the current state (refreshed whenever eps or the
+    // history change), also inside the captured CG graphs
+    const bool cons = c->cdp != nullptr;
     if (tangent)
-      kb_xfwd<1><<<grid_for(tot, kXYMinBlocks), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
-                                                                        next_counter(c), c->S, c->mt, in,
-                                                                        c->phase, c->D);
+      kb_xfwd<1><<<grid_for(tot, kXYMinBlocks), kXThreads, c->smem[BP_X], c->st>>>(
+          c->dD, c->wl, next_counter(c), c->S, c->mt, in, c->phase, c->D, cons ? c->cdp : nullptr,
+          cons ? c->ca : nullptr, cons ? c->cn : nullptr);
     else
-      kb_xfwd<0><<<grid_for(tot, kXYMinBlocks), kXThreads, c->smem[BP_X], c->st>>>(c->dD, c->wl,
-                                                                        next_counter(c), c->S, c->mt, in,
-                                                                        c->phase, c->D);
+      kb_xfwd<0><<<grid_for(tot, kXYMinBlocks), kXThreads, c->smem[BP_X], c->st>>>(
+          c->dD, c->wl, next_counter(c), c->S, c->mt, in, c->phase, c->D, nullptr, nullptr, nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (c->any3d) {
@@ -615,7 +638,8 @@ cudaError_t trial(rve_batch_ctx* c, Gate gt, const R* p, bool with_state) {
                                                        c->khist,
                                                        with_state ? c->sig : nullptr, with_state ? c->D : nullptr,
                                                        with_state ? c->sig_t : c->sig, with_state ? c->D_t : c->D,
-                                                       with_state ? c->kap_t : c->kap, c->part);
+                                                       with_state ? c->kap_t : c->kap, c->part,
+                                                       with_state ? c->cdp : nullptr, c->ca, c->cn);
   ++c->launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -741,10 +765,26 @@ rve_status batch_cg(rve_batch_ctx* c, const std::vector<char>& mask, rve_step_re
   return RVE_OK;
 }
 
+// The consistent tangent's per-voxel data for the current state (eps,
+// khist) of every member: one preparation launch per member (outside the
+// captured CG iteration; once per accepted Newton state).
+rve_status batch_refresh_hessian(rve_batch_ctx* c) {
+  if (!c->cdp) return RVE_OK;
+  const EigTable<R> none{};
+  for (int i = 0; i < c->n; ++i) {
+    const BDesc& d = c->desc[i];
+    BCK(cons_prep<R>(c->g[i], c->mt, none, c->phase + d.voff, c->eps + d.foff, c->khist + d.voff, c->cdp + d.voff,
+                     c->ca + d.foff, c->cn + d.foff, c->st, &c->launches),
+        "consistent tangent");
+  }
+  return RVE_OK;
+}
+
 rve_status batch_solve(rve_batch_ctx* c, const double* dE, rve_step_report* reps) {
   const int n = c->n;
   std::vector<char> all(n, 1);
   const Gate ga = gate_bits(all);
+  rve_status s0 = RVE_OK;
   // radius defaults per RVE (first load step)
   bool upload_r = false;
   for (int i = 0; i < n; ++i) {
@@ -775,6 +815,7 @@ rve_status batch_solve(rve_batch_ctx* c, const double* dE, rve_step_report* reps
   BCK(reset_counters(c), "memset");
   BCK((vec<V_ADDE, 0>(c, ga, c->eps, nullptr, nullptr, nullptr, nullptr, 0)), "load increment");
   BCK(trial(c, ga, nullptr, false), "stress");
+  if ((s0 = batch_refresh_hessian(c)) != RVE_OK) return s0;
   BCK(batch_apply(c, c->sig, c->gv, false, c->gv, offsetof(DevScalars, gg), ga), "gradient");
   rve_status s = read_all(c);
   if (s != RVE_OK) return s;
@@ -827,6 +868,7 @@ rve_status batch_solve(rve_batch_ctx* c, const double* dE, rve_step_report* reps
     BCK((vec<V_COPY, 0>(c, gacc, c->sig, nullptr, nullptr, c->sig_t, nullptr, 0)), "accept stress");
     BCK(scopy(c, gacc, c->D, c->D_t), "accept damage");
     BCK(scopy(c, gacc, c->kap, c->kap_t), "accept kappa");
+    if ((s = batch_refresh_hessian(c)) != RVE_OK) return s;
     BCK(batch_apply(c, c->sig, c->gv, false, c->gv, offsetof(DevScalars, gg), gacc), "gradient");
     if ((s = read_all(c)) != RVE_OK) return s;
     for (int i = 0; i < n; ++i) {
@@ -849,6 +891,7 @@ rve_status batch_solve(rve_batch_ctx* c, const double* dE, rve_step_report* reps
     BCK(seg_reduce(c, BP_VOX, 12, offsetof(DevScalars, msig)), "means");
   }
   BCK(scopy(c, gate_bits(conv), c->khist, c->kap), "commit");
+  if ((s = batch_refresh_hessian(c)) != RVE_OK) return s;
   if ((s = read_all(c)) != RVE_OK) return s;
   bool all_conv = true;
   for (int i = 0; i < n; ++i) {
@@ -869,7 +912,8 @@ void batch_free(rve_batch_ctx* c) {
   if (!c) return;
   for (auto& w : c->sw) spectral_free(w);
   void* ptrs[] = {c->dD, c->counters, c->eps, c->sig, c->sig_t, c->gv, c->z, c->r, c->d, c->Hd, c->tmp,
-                  c->D, c->D_t, c->kap, c->kap_t, c->khist, c->phase, c->S, c->part, c->dE, c->dR};
+                  c->D, c->D_t, c->kap, c->kap_t, c->khist, c->phase, c->S, c->part, c->dE, c->dR,
+                  c->cdp, c->ca, c->cn};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->dnb) cudaFree(c->dnb);
@@ -966,6 +1010,12 @@ rve_status batch_init(rve_batch_ctx* c, const int* dims, const int* ndims, const
   for (R** f : fields) BCK(cudaMalloc(f, fb), "field allocation");
   R** sfields[] = {&c->D, &c->D_t, &c->kap, &c->kap_t, &c->khist};
   for (R** f : sfields) BCK(cudaMalloc(f, vb), "scalar-field allocation");
+  if (c->opts.hessian == 1) {
+    BCK(cudaMalloc(&c->cdp, vb), "consistent-tangent allocation");
+    BCK(cudaMalloc(&c->ca, fb), "consistent-tangent allocation");
+    BCK(cudaMalloc(&c->cn, fb), "consistent-tangent allocation");
+    BCK(cudaMemsetAsync(c->cdp, 0, vb, c->st), "memset");
+  }
   BCK(cudaMalloc(&c->phase, c->nvox), "phase allocation");
   for (int i = 0; i < n; ++i)
     BCK(cudaMemcpyAsync(c->phase + c->desc[i].voff, ids[i], c->g[i].nvox, cudaMemcpyDeviceToDevice, c->st),
@@ -1136,6 +1186,14 @@ rve_status rve_batch_create(int n, const int* dims, const int* ndims, const uint
     delete c;
     return bfail(nullptr, RVE_ERR_ARG, "batched solver supports precision 32 only");
   }
+  if (c->opts.hessian != 0 && c->opts.hessian != 1) {
+    delete c;
+    return bfail(nullptr, RVE_ERR_ARG, "hessian must be 0 (secant) or 1 (symmetric consistent)");
+  }
+  if (c->opts.element != 0) {
+    delete c;
+    return bfail(nullptr, RVE_ERR_ARG, "batched solver supports element 0 only");
+  }
   rve_status s = batch_init(c, dims, ndims, phase_ids_dev, phases, nphase);
   if (s != RVE_OK) {
     g_batch_create_error = c->err;
@@ -1258,7 +1316,7 @@ rve_status rve_batch_reset(rve_batch_t c) {
   std::vector<char> all(c->n, 1);
   BCK(reset_counters(c), "memset");
   BCK(trial(c, gate_bits(all), nullptr, false), "state stress");
-  return RVE_OK;
+  return batch_refresh_hessian(c);
 }
 
 const char* rve_batch_last_error(rve_batch_t c) { return c ? c->err.c_str() : g_batch_create_error.c_str(); }

@@ -121,6 +121,47 @@ def test_batched_load_steps_match_single_contexts():
     b.close()
 
 
+def test_batched_consistent_load_steps_match_single_contexts():
+    """The same two increments with the symmetric consistent tangent as the
+    Hessian (rve_solver_opts.hessian = 1) on both sides: the batched solve
+    prepares the tangent's per-voxel data member by member and carries it
+    through the captured CG iteration; Newton iteration counts (within 1),
+    convergence and homogenised stress (1e-4 relative) as the single
+    contexts; a member that localises at the onset exhausts the Newton cap
+    on both sides."""
+    from paper_2207_10657_gb300 import RVEBatch, RVESolver, build
+    build.build()
+    rng = np.random.default_rng(4)
+    pms = [_micro(d, 40 + i) for i, d in enumerate(DIMS)]
+    dEs, frees = [], []
+    for d in DIMS:
+        nc = 3 if len(d) == 2 else 6
+        a = rng.standard_normal(nc)
+        a *= 4e-5 / np.linalg.norm(a)
+        dEs.append(list(a))
+        frees.append([0] * nc)
+    opts = dict(eta_eq=1e-6, eta_cg=1e-2, max_nr=200, hessian=1)
+    b = RVEBatch(DIMS, pms, [MATRIX, STIFF], **opts)
+    singles = [RVESolver(d, pms[i], [MATRIX, STIFF], precision=32, **opts) for i, d in enumerate(DIMS)]
+    for step in range(2):
+        reps = b.solve_step(dEs, frees, raise_on_error=False)
+        for i, s in enumerate(singles):
+            rs = s.solve_step(dEs[i], free_mask=frees[i], raise_on_error=False)
+            if step == 0:
+                assert reps[i]["converged"] and rs["converged"], (i, step, reps[i], rs)
+            assert reps[i]["converged"] == rs["converged"], (i, step, reps[i], rs)
+            if not rs["converged"]:  # localised: both sides exhaust the Newton cap
+                assert reps[i]["nr_iters"] == rs["nr_iters"] == 200
+                continue
+            assert abs(reps[i]["nr_iters"] - rs["nr_iters"]) <= 1, (i, step, reps[i], rs)
+            sb = np.array(reps[i]["mean_stress"])
+            ss = np.array(rs["mean_stress"])
+            assert np.linalg.norm(sb - ss) <= 1e-4 * np.linalg.norm(ss), (i, step, sb, ss)
+    for s in singles:
+        s.close()
+    b.close()
+
+
 def test_batched_2d_elastic_step_matches_oracle():
     """A single elastic increment on a batch of 2D cells agrees with the
     oracle's trust-region solve to the solver tolerance."""

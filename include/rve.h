@@ -57,9 +57,13 @@ typedef enum {
   RVE_ERR_OOM = -3,           /* device allocation failed */
   RVE_ERR_NOT_CONVERGED = -4, /* iteration caps reached */
   RVE_ERR_NONFINITE = -5,     /* NaN/Inf met in a reduction */
-  RVE_ERR_TIMEOUT = -6        /* reserved for a bounded device wait that gives
-                                 up; no entry point of this version waits on
-                                 the device without a bound, none returns it */
+  RVE_ERR_TIMEOUT = -6        /* a bounded device wait gave up: the x-forward
+                                 pass of 3D FP32 grids waits on an mbarrier
+                                 for its bulk tensor copies (at most about a
+                                 second); the calls that read the device
+                                 scalars back (solve steps, Steihaug, dot
+                                 products) report it.  Every device wait of the
+                                 library is bounded. */
 } rve_status;
 
 /* One material phase, indexed by the phase id stored per voxel.

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librve.so")
-SOURCES = ["hv_passes.cu", "hv_fast.cu", "hv_cluster.cu", "solver_kernels.cu", "rve_api.cu", "lbfgs.cu", "homogenize.cu",
+SOURCES = ["hv_passes.cu", "hv_fast.cu", "hv_cluster.cu", "hv_tma.cu", "solver_kernels.cu", "rve_api.cu", "lbfgs.cu", "homogenize.cu",
            "consistent.cu", "noalloc.cu", "batch.cu", "fno.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -15,6 +15,7 @@
 #include "hv_cluster.cuh"
 #include "hv_fast.cuh"
 #include "hv_passes.cuh"
+#include "hv_tma.cuh"
 #include "passes_generic.cuh"
 #include "project.cuh"
 
@@ -280,8 +281,12 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
       fwd_dot = want && e == cudaSuccess;
     } else if (!w.generic && fast_size(g.nx)) {
       const bool want = mode == XIn::Tangent && dot_with != nullptr && dot_with == in && !w.unfused;
-      e = fast_xfwd(g, in, phase, damage, mt, w.spec, w.tw[0], mode == XIn::Tangent, want ? w.partials : nullptr,
-                    &fwd_blocks, st, &w.cons);
+      if (!(mode == XIn::Tangent && w.cons.dp != nullptr))
+        e = tma_xfwd(g, in, phase, damage, mt, w.spec, w.tw[0], mode == XIn::Tangent, want ? w.partials : nullptr,
+                     &fwd_blocks, st, w.wait_err);
+      if (e == cudaErrorNotSupported)
+        e = fast_xfwd(g, in, phase, damage, mt, w.spec, w.tw[0], mode == XIn::Tangent, want ? w.partials : nullptr,
+                      &fwd_blocks, st, &w.cons);
       fwd_dot = want && e == cudaSuccess;
     }
   }
@@ -348,7 +353,11 @@ cudaError_t spectral_hv_cg(const GridDesc& g, SpecWork<float>& w, const MatTable
       e = cluster_xyfwd(g, d, phase, damage, mt, w.spec, w.tw[0], w.twq, true, w.partials, st);
       fb = cluster_blocks(g);
     } else {
-      e = fast_xfwd(g, d, phase, damage, mt, w.spec, w.tw[0], true, w.partials, &fb, st, &w.cons);
+      e = w.cons.dp == nullptr ? tma_xfwd(g, d, phase, damage, mt, w.spec, w.tw[0], true, w.partials, &fb, st,
+                                          w.wait_err)
+                               : cudaErrorNotSupported;
+      if (e == cudaErrorNotSupported)
+        e = fast_xfwd(g, d, phase, damage, mt, w.spec, w.tw[0], true, w.partials, &fb, st, &w.cons);
     }
   }
   if (e != cudaSuccess) return e;

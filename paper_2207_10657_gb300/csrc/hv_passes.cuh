@@ -48,6 +48,7 @@ template <typename R> struct SpecWork {
   bool unfused = false;        // true: compiled passes, but CG scalars and updates as the generic path
   bool cluster = false;        // true: the cluster x+y passes where they apply (opt-in: slower, see hv_cluster.cu)
   Cx<R>* twq = nullptr;        // e^{-2 pi i t / (Nx/4)}: the cluster passes' y sub-transform
+  int* wait_err = nullptr;     // device word a kernel sets when a bounded wait runs out (NULL: no TMA passes)
 };
 
 enum class XIn { Plain = 0, Tangent = 1 };

@@ -54,6 +54,11 @@ template <int N, int NROW> struct RowItems {
 
 
 // ------------------------------------------------------------ x forward
+template <int N, int NC>
+__device__ __forceinline__ void xfwd_fft_store(float2* buf, float2* __restrict__ spec, const long long nrows,
+                                               const float2* __restrict__ tw, const long long row0,
+                                               const long long row_end);
+
 // One x-forward tile: the voxel rows [row0, row_end) (at most xq rows),
 // tangent applied on load, forward FFT of the real rows packed in pairs,
 // half spectrum stored.  Returns this thread's share of in : (tangent : in)
@@ -152,13 +157,25 @@ __device__ __forceinline__ float xfwd_rows(float2* buf, const float* __restrict_
     }
   }
   __syncthreads();
+  xfwd_fft_store<N, NC>(buf, spec, nrows, tw, row0, row_end);
+  return acc;
+}
+
+// The FFT and store stage of an x-forward tile whose NC * xq rows sit packed
+// in pairs in `buf` (element x of line p at x * NL + p; the caller has
+// synchronised): forward FFT of every line, then the two real rows of every
+// line separated (Hermitian symmetry of real-input spectra) and their half
+// spectra stored.  Thread t takes bin k = t mod (N/2) of the lines
+// p = t div (N/2) + j (256 / (N/2)); the Nyquist bin of every line goes to
+// threads 0 .. NL-1.  Row and component of the two halves follow from p
+// alone, so no per-item division by the half-spectrum length.
+template <int N, int NC>
+__device__ __forceinline__ void xfwd_fft_store(float2* buf, float2* __restrict__ spec, const long long nrows,
+                                               const float2* __restrict__ tw, const long long row0,
+                                               const long long row_end) {
+  constexpr int Q = xq<N, NC>();
+  constexpr int NL = NC * Q / 2;
   fft_ct<N, NL, kFT, false>(buf, tw);
-  // Separate the two real rows of every packed line (Hermitian symmetry of
-  // real-input spectra) and store the half spectra.  Thread t takes bin
-  // k = t mod (N/2) of the lines p = t div (N/2) + j (256 / (N/2)); the
-  // Nyquist bin of every line goes to threads 0 .. NL-1.  Row and component
-  // of the two halves follow from p alone, so no per-item division by the
-  // half-spectrum length.
   constexpr int NXH = N / 2 + 1;
   constexpr int KB = N / 2, GB = kFT / KB, JB = (NL + GB - 1) / GB;
   const long long plane = nrows * NXH;
@@ -193,7 +210,6 @@ __device__ __forceinline__ float xfwd_rows(float2* buf, const float* __restrict_
       }
     }
   }
-  return acc;
 }
 
 // ------------------------------------------------------------ x inverse

@@ -152,6 +152,7 @@ rve_status read_scalars(rve_ctx* c) {
   CK(cudaMemcpyAsync(c->Sh, m->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->st), "read scalars");
   CK(cudaStreamSynchronize(c->st), "synchronize");
   ++c->host_syncs;
+  if (c->Sh->wait_err) return fail(c, RVE_ERR_TIMEOUT, "a pass's bulk copies did not arrive within the wait limit");
   return RVE_OK;
 }
 
@@ -208,6 +209,7 @@ rve_status create_impl(rve_ctx* c, const uint8_t* phase_ids, const rve_phase* ph
   const long long nv = c->gs.nvox;
   CK(cudaMalloc(&m->phase, g.nvox), "phase allocation");
   CK(cudaMalloc(&m->S, sizeof(DevScalars)), "scalar allocation");
+  m->sw.wait_err = &m->S->wait_err;
   CK(cudaMemsetAsync(m->S, 0, sizeof(DevScalars), c->st), "memset");
   for (int q = 0; q < c->gs.nq; ++q)
     CK(cudaMemcpyAsync(m->phase + q * nv, phase_ids, nv, cudaMemcpyDeviceToDevice, c->st), "phase copy");

@@ -36,7 +36,8 @@ struct DevScalars {
   double sp, stp, pBp, sts, pp, ee;  // group T: trial-state sums
   double gg;                         // |G sigma|^2
   double rho, dm, dW;
-  int accept, on_boundary, nonfinite, pad1;
+  int accept, on_boundary, nonfinite;
+  int wait_err;  // set by a kernel whose bounded wait on its copies ran out
   // homogenised fields (group M: ncomp sums of sigma then ncomp of eps)
   double msig[6], meps[6];
 };

@@ -38,11 +38,12 @@ def _rel(a, b):
 
 
 # generic-engine sizes, the compile-time-specialised FP32 sizes (32..512,
-# 96/192/384) and mixtures of both, degenerate 2-point axes and a 1024 axis
+# 96/192/384; in 3D with Nx <= 256 the x-forward stages its rows by bulk
+# tensor copies) and mixtures of both, degenerate 2-point axes and a 1024 axis
 GRIDS = [(32, 24), (30, 40), (2, 2), (1024, 8), (8, 12, 10), (16, 16, 16), (24, 20, 18), (2, 2, 2),
          (6, 4, 1024), (96, 64), (512, 32), (32, 32, 32), (64, 32, 96), (128, 192, 8), (384, 6, 4),
          (8, 10, 512), (256, 8, 128), (512, 4, 8), (8, 128, 256), (4, 512, 64), (64, 64, 64), (4, 6, 384),
-         (6, 4, 192), (4, 384, 6), (6, 96, 96)]
+         (6, 4, 192), (4, 384, 6), (6, 96, 96), (96, 10, 6), (192, 6, 4)]
 
 
 @pytest.mark.parametrize("precision", [32, 64])
@@ -65,7 +66,8 @@ def test_project_matches_oracle(dims, precision):
 @pytest.mark.parametrize("precision", [32, 64])
 @pytest.mark.parametrize("dims", [(32, 24), (64, 30), (8, 12, 10), (16, 16, 16), (24, 20, 18), (40, 36, 12),
                                   (64, 64), (256, 96), (32, 32, 32), (64, 96, 32), (128, 64, 64),
-                                  (256, 8, 128), (8, 128, 256), (512, 4, 64), (64, 64, 64)])
+                                  (256, 8, 128), (8, 128, 256), (512, 4, 64), (64, 64, 64), (96, 10, 6),
+                                  (192, 6, 4)])
 def test_hessp_matches_oracle(dims, precision):
     nd = len(dims)
     nc = 3 if nd == 2 else 6

@@ -250,4 +250,69 @@ __device__ __forceinline__ void block_sum(double (&v)[NS], double* sh) {
   __syncthreads();
 }
 
+// out[s] = sum_b part[b * NS + s], s < NS, summed by one block as the
+// separate reduction kernel k_reduce_partials does -- thread t < 256 (every
+// thread of a smaller block) adds blocks t, t + 256, ... in that order, then
+// the block-wide FP64 sum -- so the results agree bit for bit.  The NS sums
+// share one sweep whose loads are issued U blocks at a time: ten thousand
+// partials cost a few L2 round trips rather than one per partial.  The
+// partials are read through L2 (other blocks of the grid wrote them).
+// Called by every thread of the block; `sh` holds NS * 32 doubles, free on
+// entry; thread 0 writes out.
+template <int NS>
+__device__ void block_reduce_partials(const double* part, int nblocks, double* out, double* sh) {
+  constexpr int U = 8;
+  const int stride = blockDim.x < 256 ? (int)blockDim.x : 256;
+  double acc[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) acc[s] = 0.0;
+  if ((int)threadIdx.x < stride) {
+    int b = threadIdx.x;
+#pragma unroll 1
+    for (; b + (U - 1) * stride < nblocks; b += U * stride) {
+      double v[U][NS];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int s = 0; s < NS; ++s) v[u][s] = __ldcg(part + (long long)(b + u * stride) * NS + s);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int s = 0; s < NS; ++s) acc[s] += v[u][s];
+    }
+#pragma unroll 1
+    for (; b < nblocks; b += stride)
+#pragma unroll
+      for (int s = 0; s < NS; ++s) acc[s] += __ldcg(part + (long long)b * NS + s);
+  }
+  block_sum<NS>(acc, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) out[s] = acc[s];
+  }
+}
+
+// Called by every thread of every block once thread 0 has written the
+// block's NS partial sums to part[block * NS + s].  The last block to arrive
+// (thread 0 fences its partials, then one atomic on `counter`) sums them with
+// block_reduce_partials, resets the counter for the next launch and returns
+// true; the other blocks return false.  No block waits on another.  Meant
+// for grids of a few hundred blocks: the fence holds thread 0 until its
+// stores are visible, which a grid of many short-lived blocks would pay once
+// per block.  `sh` holds NS * 32 doubles, free on entry.
+template <int NS>
+__device__ bool reduce_in_last_block(const double* part, int nblocks, double* out, unsigned* counter, double* sh) {
+  __shared__ unsigned s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(counter, 1u) == (unsigned)nblocks - 1u ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  block_reduce_partials<NS>(part, nblocks, out, sh);
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
 }  // namespace rve

@@ -18,6 +18,8 @@
 #include "hv_tma.cuh"
 #include "passes_generic.cuh"
 #include "project.cuh"
+#include "scalar_logic.cuh"
+#include "solver_kernels.cuh"
 
 namespace rve {
 
@@ -338,15 +340,29 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
   return cudaSuccess;
 }
 
+// Single-block launches (256 threads): a CG pass's block sums reduced into
+// the device scalars, then the scalar step of Algorithm 1 that needs them.
+__global__ void __launch_bounds__(256) k_reduce_alpha(const double* __restrict__ part, int nb, DevScalars* S) {
+  __shared__ double sh[32];
+  block_reduce_partials<1>(part, nb, &S->dHd, sh);
+  if (threadIdx.x == 0) cg_alpha_scalars(S);
+}
+
+__global__ void __launch_bounds__(256) k_reduce_beta(const double* __restrict__ part, int nb, DevScalars* S) {
+  __shared__ double sh[3 * 32];
+  block_reduce_partials<3>(part, nb, &S->rr_new, sh);
+  if (threadIdx.x == 0) cg_beta_scalars(S);
+}
+
 cudaError_t spectral_hv_cg(const GridDesc& g, SpecWork<float>& w, const MatTable<float>& mt, const float* d,
-                           const uint8_t* phase, const float* damage, float* z, float* r, double* dHd,
-                           cudaError_t (*between)(void*), void* between_arg, const int* status, const double* alpha,
-                           const double* tau, double* sums, cudaStream_t st, long long* nlaunch) {
+                           const uint8_t* phase, const float* damage, float* z, float* r, DevScalars* S,
+                           cudaStream_t st, long long* nlaunch) {
   if (w.generic || w.unfused || !fast_size(g.nx)) return cudaErrorNotSupported;
   long long nl = 0;
   cudaError_t e;
   int fb = 0, ib = 0;
   const bool cl = use_cluster(g, w), cl_fwd = cl && w.cons.dp == nullptr;
+  bool fwd_reduced = false;  // d:H:d and the step length done by the x-forward launch
   {
     PassScope ps(w.timer, st, PASS_XFWD);
     if (cl_fwd) {
@@ -354,29 +370,35 @@ cudaError_t spectral_hv_cg(const GridDesc& g, SpecWork<float>& w, const MatTable
       fb = cluster_blocks(g);
     } else {
       e = w.cons.dp == nullptr ? tma_xfwd(g, d, phase, damage, mt, w.spec, w.tw[0], true, w.partials, &fb, st,
-                                          w.wait_err)
+                                          w.wait_err, S)
                                : cudaErrorNotSupported;
+      fwd_reduced = e == cudaSuccess;
       if (e == cudaErrorNotSupported)
         e = fast_xfwd(g, d, phase, damage, mt, w.spec, w.tw[0], true, w.partials, &fb, st, &w.cons);
     }
   }
   if (e != cudaSuccess) return e;
   ++nl;
-  if ((e = reduce_partials(w.partials, fb, 1, dHd, st, &nl)) != cudaSuccess) return e;
+  if (!fwd_reduced) {
+    k_reduce_alpha<<<1, 256, 0, st>>>(w.partials, fb, S);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++nl;
+  }
   if ((e = spectral_middle<float>(g, w, st, &nl, cl_fwd, cl)) != cudaSuccess) return e;
-  if ((e = between(between_arg)) != cudaSuccess) return e;
   {
     PassScope ps(w.timer, st, PASS_XINV);
     if (cl) {
-      e = cluster_yxinv_cg(g, w.spec, z, r, d, status, alpha, tau, w.partials, w.tw[0], w.twq, st);
+      e = cluster_yxinv_cg(g, w.spec, z, r, d, &S->status, &S->alpha, &S->tau, w.partials, w.tw[0], w.twq, st);
       ib = cluster_blocks(g);
     } else {
-      e = fast_xinv_cg(g, w.spec, z, r, d, status, alpha, tau, w.partials, w.tw[0], &ib, st);
+      e = fast_xinv_cg(g, w.spec, z, r, d, &S->status, &S->alpha, &S->tau, w.partials, w.tw[0], &ib, st);
     }
   }
   if (e != cudaSuccess) return e;
   ++nl;
-  if ((e = reduce_partials(w.partials, ib, 3, sums, st, &nl)) != cudaSuccess) return e;
+  k_reduce_beta<<<1, 256, 0, st>>>(w.partials, ib, S);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ++nl;
   if (nlaunch) *nlaunch += nl;
   return cudaSuccess;
 }

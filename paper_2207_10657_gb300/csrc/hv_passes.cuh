@@ -60,17 +60,21 @@ cudaError_t spectral_apply(const GridDesc& g, SpecWork<R>& w, const MatTable<R>&
                            const uint8_t* phase, const R* damage, XIn mode, R* out,
                            const R* dot_with, double* dot_out, cudaStream_t st, long long* nlaunch);
 
-// One Steihaug-CG product step on the compiled FP32 x passes: forward
-// passes with d:H:d formed in the x-forward pass (into *dHd), then
-// `between` (the CG step-length kernel, run on `st` once d:H:d is known),
-// then the x-inverse applying z += alpha d, r += alpha Hd (or z += tau d on
-// an exit) from the device scalars *status / *alpha / *tau, with r'.r',
-// r'.r, z'.z into sums[0..2].  Hd is never stored.  Returns
-// cudaErrorNotSupported (nothing launched) when Nx has no compiled pass.
+struct DevScalars;  // solver_kernels.cuh
+
+// One Steihaug-CG iteration's product on the compiled FP32 x passes, on the
+// device scalars S: the forward passes with d:H:d formed in the x-forward
+// pass (into S->dHd), then Algorithm 1's step length, then the x-inverse
+// applying z += alpha d, r += alpha Hd (or z += tau d on an exit) with
+// r'.r', r'.r, z'.z into S->rr_new, S->rnr, S->zz_new, then the convergence
+// / beta decision.  Hd is never stored.  The persistent x-forward pass
+// reduces d:H:d and takes the step-length decision in its last block; else
+// one single-block kernel does both, as one does after the x-inverse.
+// Returns cudaErrorNotSupported (nothing launched) when Nx has no compiled
+// pass.
 cudaError_t spectral_hv_cg(const GridDesc& g, SpecWork<float>& w, const MatTable<float>& mt, const float* d,
-                           const uint8_t* phase, const float* damage, float* z, float* r, double* dHd,
-                           cudaError_t (*between)(void*), void* between_arg, const int* status, const double* alpha,
-                           const double* tau, double* sums, cudaStream_t st, long long* nlaunch);
+                           const uint8_t* phase, const float* damage, float* z, float* r, DevScalars* S,
+                           cudaStream_t st, long long* nlaunch);
 
 template <typename R>
 cudaError_t spectral_setup(const GridDesc& g, SpecWork<R>& w);

@@ -22,6 +22,7 @@
 
 #include "hv_tiles.cuh"
 #include "hv_tma.cuh"
+#include "scalar_logic.cuh"
 
 namespace rve {
 namespace {
@@ -88,13 +89,15 @@ __device__ __noinline__ void tma_fft_store(float2* buf, float2* spec, const long
 }
 
 // MODE 0: plain (the gradient G : sigma); 1: secant tangent, with this
-// CTA's share of in : (tangent : in) in partials[blockIdx.x] when set.
+// CTA's share of in : (tangent : in) in partials[blockIdx.x] when set; with
+// S as well, the last CTA to finish sums the shares into S->dHd and takes
+// Algorithm 1's step-length decision.
 template <int N, int MODE>
 __global__ void __launch_bounds__(kFT, kTmaBlocksPerSM)
     kt_xfwd(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_dmg,
             const __grid_constant__ CUtensorMap tm_ph, const MatTable<float> mt, float2* __restrict__ spec,
             const long long nrows, const float2* __restrict__ tw, double* __restrict__ partials, const int ntiles,
-            int* __restrict__ wait_err) {
+            int* __restrict__ wait_err, DevScalars* __restrict__ S) {
   using L = TmaLayout<N>;
   constexpr int Q = L::Q, NL = L::NL;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -134,7 +137,7 @@ __global__ void __launch_bounds__(kFT, kTmaBlocksPerSM)
         atomicExch(wait_err, 1);
         mbar_wait(&bar, parity);  // once more, bounded: the copies in flight target this CTA's memory
       }
-      return;
+      break;  // still arrives at the reduction below, so its counter stays consistent
     }
     // tangent from the staged rows, scattered into the packed FFT lines;
     // consecutive threads take consecutive x
@@ -188,6 +191,8 @@ __global__ void __launch_bounds__(kFT, kTmaBlocksPerSM)
     double vv[1] = {acc};
     block_sum<1>(vv, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = vv[0];
+    if (S && reduce_in_last_block<1>(partials, gridDim.x, &S->dHd, &S->red_cnt[0], red) && threadIdx.x == 0)
+      cg_alpha_scalars(S);
   }
 }
 
@@ -226,7 +231,7 @@ bool encode(CUtensorMap* m, CUtensorMapDataType dt, cuuint32_t rank, const void*
 template <int N>
 cudaError_t tma_xfwd_n(const GridDesc& g, const float* in, const uint8_t* phase, const float* dmg,
                        const MatTable<float>& mt, float2* spec, const float2* tw, bool tangent, double* partials,
-                       int* nblocks, cudaStream_t st, int* wait_err) {
+                       int* nblocks, cudaStream_t st, int* wait_err, DevScalars* S) {
   using L = TmaLayout<N>;
   constexpr int Q = L::Q;
   // the copies' alignment rules: 16-byte base addresses, row strides and box
@@ -260,9 +265,10 @@ cudaError_t tma_xfwd_n(const GridDesc& g, const float* in, const uint8_t* phase,
     if (dev >= 0 && dev < 64) attr[mi][dev] = 1;
   }
   if (tangent)
-    kt_xfwd<N, 1><<<grid, kFT, smem, st>>>(tin, tdm, tph, mt, spec, g.nrows, tw, partials, ntiles, wait_err);
+    kt_xfwd<N, 1><<<grid, kFT, smem, st>>>(tin, tdm, tph, mt, spec, g.nrows, tw, partials, ntiles, wait_err,
+                                           partials ? S : nullptr);
   else
-    kt_xfwd<N, 0><<<grid, kFT, smem, st>>>(tin, tdm, tph, mt, spec, g.nrows, tw, nullptr, ntiles, wait_err);
+    kt_xfwd<N, 0><<<grid, kFT, smem, st>>>(tin, tdm, tph, mt, spec, g.nrows, tw, nullptr, ntiles, wait_err, nullptr);
   *nblocks = grid;
   return cudaGetLastError();
 }
@@ -271,10 +277,10 @@ cudaError_t tma_xfwd_n(const GridDesc& g, const float* in, const uint8_t* phase,
 
 cudaError_t tma_xfwd(const GridDesc& g, const float* in, const uint8_t* phase, const float* dmg,
                      const MatTable<float>& mt, float2* spec, const float2* tw, bool tangent, double* partials,
-                     int* nblocks, cudaStream_t st, int* wait_err) {
+                     int* nblocks, cudaStream_t st, int* wait_err, DevScalars* S) {
   if (g.ndim != 3 || g.ncomp != 6 || g.nq != 1 || !wait_err || !encoder()) return cudaErrorNotSupported;
 #define RVE_CASE(n_) \
-  if (g.nx == n_) return tma_xfwd_n<n_>(g, in, phase, dmg, mt, spec, tw, tangent, partials, nblocks, st, wait_err);
+  if (g.nx == n_) return tma_xfwd_n<n_>(g, in, phase, dmg, mt, spec, tw, tangent, partials, nblocks, st, wait_err, S);
   RVE_CASE(32) RVE_CASE(64) RVE_CASE(96) RVE_CASE(128) RVE_CASE(192) RVE_CASE(256)
 #undef RVE_CASE
   return cudaErrorNotSupported;

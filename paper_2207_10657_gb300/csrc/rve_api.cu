@@ -231,18 +231,6 @@ rve_status create_impl(rve_ctx* c, const uint8_t* phase_ids, const rve_phase* ph
   return RVE_OK;
 }
 
-// The CG step-length kernel, launched between the forward and the inverse
-// passes of the fused product.
-struct AlphaArg {
-  DevScalars* S;
-  cudaStream_t st;
-  long long* nl;
-};
-static cudaError_t launch_alpha(void* p) {
-  AlphaArg* a = static_cast<AlphaArg*>(p);
-  return cg_alpha(a->S, a->st, a->nl);
-}
-
 // One iteration of Algorithm 1 after the direction d is known: the product
 // H d with the step length and the iterate / residual update (fused into
 // the compiled FP32 passes, else the generic product, step length and
@@ -253,9 +241,7 @@ cudaError_t issue_cg_iteration(rve_ctx* c, cudaStream_t st, long long* nl) {
   const GridDesc& g = c->g;
   cudaError_t e = cudaErrorNotSupported;
   if constexpr (std::is_same<R, float>::value) {
-    AlphaArg aa{m->S, st, nl};
-    e = spectral_hv_cg(c->gs, m->sw, m->mt, m->d, m->phase, m->D, m->z, m->r, &m->S->dHd, launch_alpha, &aa,
-                       &m->S->status, &m->S->alpha, &m->S->tau, &m->S->rr_new, st, nl);
+    e = spectral_hv_cg(c->gs, m->sw, m->mt, m->d, m->phase, m->D, m->z, m->r, m->S, st, nl);
   }
   if (e == cudaErrorNotSupported) {
     e = spectral_apply<R>(c->gs, m->sw, m->mt, m->d, m->phase, m->D, XIn::Tangent, m->Hd, m->d, &m->S->dHd, st, nl);
@@ -264,8 +250,8 @@ cudaError_t issue_cg_iteration(rve_ctx* c, cudaStream_t st, long long* nl) {
       PassScope ps(&c->timer, st, PASS_CGVEC);
       e = cg_update<R>(g, m->z, m->r, m->d, m->Hd, m->S, m->sw.partials, st, nl);
     }
+    if (e == cudaSuccess) e = cg_beta(m->S, st, nl);
   }
-  if (e == cudaSuccess) e = cg_beta(m->S, st, nl);
   if (e == cudaSuccess) {
     PassScope ps(&c->timer, st, PASS_CGVEC);
     e = cg_dupdate<R>(g, m->z, m->r, m->d, m->S, m->sw.partials, st, nl);

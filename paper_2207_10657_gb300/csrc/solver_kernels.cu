@@ -149,11 +149,13 @@ __global__ void k_cg_restart_s(DevScalars* S) { cg_restart_scalars(S); }
 template <typename R>
 __global__ void __launch_bounds__(kVThreads)
     k_cg_dupdate(long long n, const R* __restrict__ z, const R* __restrict__ r, R* __restrict__ d,
-                 const DevScalars* __restrict__ S, double* __restrict__ part) {
+                 DevScalars* __restrict__ S, double* __restrict__ part) {
   // Algorithm 1 continues only while running without a pending restart: a
   // device-side loop reaches this kernel after every iteration, the host
   // loop only in that case.  (Skipped, the sums of group D go stale; they
   // are recomputed by the update after the restart and unused on exit.)
+  // Every block takes the same decision: nothing in the launch writes status
+  // or restart.
   if (S->status != CG_RUN || S->restart) return;
   const R beta = (R)S->beta;
   KSum<R> acc[3];
@@ -188,6 +190,9 @@ __global__ void __launch_bounds__(kVThreads)
     }
   }
   finish_sums<R, 3>(acc, part);
+  // group D (dd, zd, rd) summed by the last block to finish
+  __shared__ double rsh[3 * 32];
+  reduce_in_last_block<3>(part, gridDim.x, &S->dd, &S->red_cnt[1], rsh);
 }
 
 // ------------------------------------------------------- constitutive
@@ -377,9 +382,8 @@ cudaError_t cg_dupdate(const GridDesc& g, const R* z, const R* r, R* d, DevScala
                        cudaStream_t st, long long* nl) {
   const long long n = g.nvox * g.ncomp;
   k_cg_dupdate<R><<<kVBlocks, kVThreads, 0, st>>>(n, z, r, d, S, part);
-  RVE_TRY(cudaGetLastError());
   *nl += 1;
-  return reduce_partials(part, kVBlocks, 3, &S->dd, st, nl);
+  return cudaGetLastError();
 }
 
 template <typename R>

@@ -38,6 +38,9 @@ struct DevScalars {
   double rho, dm, dW;
   int accept, on_boundary, nonfinite;
   int wait_err;  // set by a kernel whose bounded wait on its copies ran out
+  // arrival counters of the reductions done by a launch's last block (d:H:d
+  // in the x-forward pass, group D in the direction update)
+  unsigned red_cnt[2];
   // homogenised fields (group M: ncomp sums of sigma then ncomp of eps)
   double msig[6], meps[6];
 };
@@ -74,7 +77,7 @@ cudaError_t cg_beta(DevScalars* S, cudaStream_t st, long long* nl);
 template <typename R>
 cudaError_t cg_restart(const GridDesc& g, R* r, const R* Hz, const R* gvec, DevScalars* S, double* part,
                        cudaStream_t st, long long* nl);
-// d = -r + beta d; sums group D.
+// d = -r + beta d; sums group D (reduced inside the same launch).
 template <typename R>
 cudaError_t cg_dupdate(const GridDesc& g, const R* z, const R* r, R* d, DevScalars* S, double* part,
                        cudaStream_t st, long long* nl);
